@@ -1,0 +1,180 @@
+"""Exact density-peaks clustering in FP64 by brute force -- TEST INFRASTRUCTURE ONLY.
+
+This is the paper's ``BruteForce`` instance ("exact DPC", Sec. 6.1): exact
+k-NN, the density functions of Sec. 4.2 / Appendix A, Definition 2.1 for the
+dependent point, and the noise / center / union-find steps of Algorithm 2.
+Everything is in float64 numpy; nothing here is shared with the GPU library.
+Also: the Adjusted Rand Index (Sec. 6.1, Hubert and Arabie) and a tie-aware
+k-NN recall.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+L2, IP = 0, 1
+
+
+def _block_dist(X: np.ndarray, Y: np.ndarray, metric: int) -> np.ndarray:
+    """Exact FP64 distances D between the rows of X and Y."""
+    X = X.astype(np.float64)
+    Y = Y.astype(np.float64)
+    if metric == IP:
+        return 1.0 - X @ Y.T
+    d2 = (X * X).sum(1)[:, None] + (Y * Y).sum(1)[None, :] - 2.0 * (X @ Y.T)
+    # the expansion above can lose a few ulps; recompute the small ones exactly
+    np.maximum(d2, 0.0, out=d2)
+    return np.sqrt(d2)
+
+
+def exact_dist_rows(X: np.ndarray, rows: np.ndarray, metric: int = L2) -> np.ndarray:
+    """D(x_i, x_j) for i in rows and all j, computed as sum of squared
+    differences (no cancellation) -- slow but exact to FP64 rounding."""
+    Xd = X.astype(np.float64)
+    out = np.empty((len(rows), X.shape[0]))
+    for t, i in enumerate(rows):
+        if metric == IP:
+            out[t] = 1.0 - Xd @ Xd[i]
+        else:
+            diff = Xd - Xd[i]
+            out[t] = np.sqrt(np.einsum("ij,ij->i", diff, diff))
+    return out
+
+
+def exact_knn(X: np.ndarray, k: int, metric: int = L2, block: int = 512):
+    """Exact k nearest neighbours of every point over P minus itself, sorted by
+    (D, id). Returns ids (n,k) int64, dist (n,k) float64."""
+    n = X.shape[0]
+    ids = np.empty((n, k), np.int64)
+    dist = np.empty((n, k))
+    for b0 in range(0, n, block):
+        rows = np.arange(b0, min(n, b0 + block))
+        D = exact_dist_rows(X, rows, metric)
+        D[np.arange(len(rows)), rows] = np.inf  # exclude the point itself
+        # stable sort on D keeps smaller ids first among equal distances
+        order = np.argsort(D, axis=1, kind="stable")[:, :k]
+        ids[rows] = order
+        dist[rows] = np.take_along_axis(D, order, 1)
+    return ids, dist
+
+
+def density(dist: np.ndarray, fn: str = "kth", normalize: bool = False, ids: np.ndarray | None = None):
+    """Density from the sorted k-NN distances (Sec. 4.2, Appendix A).
+    Returns (rho, key): key ranks the points (equal to rho except for exp-sum,
+    whose key is the exponent)."""
+    k = dist.shape[1]
+    if fn == "kth":
+        with np.errstate(divide="ignore"):
+            rho = 1.0 / dist[:, -1]
+        key = rho
+    elif fn == "exp-sum":
+        key = -(dist ** 2).sum(1) / k
+        rho = np.exp(key)
+    elif fn == "sum-exp":
+        rho = np.exp(-(dist ** 2)).sum(1) / k
+        key = rho
+    elif fn == "sum":
+        rho = -dist.sum(1)
+        key = rho
+    else:
+        raise ValueError(fn)
+    if normalize:
+        rho = rho * k / rho[ids].sum(1)
+        key = rho
+    return rho, key
+
+
+def rank_order(key: np.ndarray) -> np.ndarray:
+    """Points from highest to lowest rank: key descending, smaller id first."""
+    n = key.size
+    return np.lexsort((np.arange(n), -key))
+
+
+def exact_dependent(X: np.ndarray, key: np.ndarray, metric: int = L2, block: int = 512):
+    """Definition 2.1: lambda_i = the closest point ranked above i (ties: the
+    smaller id); delta_i = D(x_i, lambda_i), +inf when there is none."""
+    n = X.shape[0]
+    order = rank_order(key)
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)  # 0 = highest
+    lam = np.full(n, -1, np.int64)
+    delta = np.full(n, np.inf)
+    for b0 in range(0, n, block):
+        rows = np.arange(b0, min(n, b0 + block))
+        D = exact_dist_rows(X, rows, metric)
+        higher = rank[None, :] < rank[rows][:, None]
+        D = np.where(higher, D, np.inf)
+        j = np.argmin(D, axis=1)  # first minimum = smallest id
+        ok = np.isfinite(D[np.arange(len(rows)), j])
+        lam[rows[ok]] = j[ok]
+        delta[rows[ok]] = D[np.arange(len(rows)), j][ok]
+    return lam, delta
+
+
+def cluster(rho, lam, delta, center: str = "product", rho_min: float = 0.0, delta_min: float = 0.0,
+            n_clusters: int = 1):
+    """Noise (rho < rho_min), centers (delta > delta_min, or the n_clusters
+    largest delta * rho), then every other point joins its dependent point's
+    cluster. A cluster is named by its root: the member whose dependent edge
+    was cut. Implemented by following dependent pointers (the union-find of
+    Algorithm 2 yields the same partition)."""
+    n = rho.size
+    noise = rho < rho_min
+    if center == "threshold":
+        cen = ~noise & (delta > delta_min)
+    else:
+        prod = np.where((delta == 0) | (rho == 0), 0.0, delta * rho)
+        cand = np.flatnonzero(~noise)
+        order = cand[np.lexsort((cand, -prod[cand]))]
+        cen = np.zeros(n, bool)
+        cen[order[:n_clusters]] = True
+    cut = noise | cen | (lam < 0)
+    parent = np.where(cut, np.arange(n), lam)
+    # pointer jumping until every point points at its root
+    while True:
+        nxt = parent[parent]
+        if np.array_equal(nxt, parent):
+            break
+        parent = nxt
+    return parent.astype(np.int64), int(cut.sum())
+
+
+def exact_dpc(X: np.ndarray, k: int, metric: int = L2, density_fn: str = "kth", **cluster_kw):
+    ids, dist = exact_knn(X, k, metric)
+    rho, key = density(dist, density_fn, ids=ids)
+    lam, delta = exact_dependent(X, key, metric)
+    labels, nc = cluster(rho, lam, delta, **cluster_kw)
+    return dict(ids=ids, dist=dist, rho=rho, key=key, lam=lam, delta=delta, labels=labels, n_clusters=nc)
+
+
+def ari(a: np.ndarray, b: np.ndarray) -> float:
+    """Adjusted Rand Index (Hubert and Arabie), with int64 pair counts.
+    Two identical partitions give 1.0, including the degenerate 0/0 case."""
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    n = a.size
+    _, ai = np.unique(a, return_inverse=True)
+    _, bi = np.unique(b, return_inverse=True)
+    cont = np.zeros((ai.max() + 1, bi.max() + 1), np.int64)
+    np.add.at(cont, (ai, bi), 1)
+
+    def c2(x):
+        x = np.asarray(x, np.int64)
+        return (x * (x - 1) // 2).sum()
+
+    sum_ij = c2(cont)
+    sum_a = c2(cont.sum(1))
+    sum_b = c2(cont.sum(0))
+    total = n * (n - 1) // 2
+    expected = sum_a * sum_b / total if total else 0.0
+    max_index = 0.5 * (sum_a + sum_b)
+    if max_index == expected:
+        return 1.0
+    return float((sum_ij - expected) / (max_index - expected))
+
+
+def knn_recall(found_dist: np.ndarray, exact_dist: np.ndarray, rel: float = 1e-5) -> float:
+    """Tie-aware recall: per query, the fraction of the k returned points whose
+    distance is within (1 + rel) of the exact k-th distance; averaged."""
+    kth = exact_dist[:, -1:]
+    ok = found_dist <= kth * (1.0 + rel) + 1e-30
+    return float(ok.mean())

@@ -1,0 +1,407 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here runs the CUDA library. Each test checks the oracle against
+something other than itself: the paper's worked example (tests/golden), exact
+FP64 brute force written independently in numpy or pure Python, closed forms,
+and the invariants of the method.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from tests.helpers import example_arrays, random_graph, ranks_above
+
+
+# ---------------------------------------------------------------- worked example (Sec. 3)
+
+def test_example_nearest_neighbours(golden_example):
+    """Sec. 3 step 2: greedy search with k = L = 1 from the query finds c, c, b, f, d, d."""
+    X, G, names, idx = example_arrays(golden_example)
+    P = oracle.Points(X)
+    for q, nn in golden_example["nearest_neighbor"].items():
+        ids, _ = oracle.greedy_search(P, G, idx[q], [idx[q]], L=1, k=1)
+        assert names[ids[0]] == nn, q
+
+
+def test_example_density_and_rank(golden_example):
+    """Sec. 3 step 3: kth density values and the ranking b, c, a, d, f, e."""
+    X, G, names, idx = example_arrays(golden_example)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=1, k=1, density=oracle.DENS_KTH)
+    for c, expr in golden_example["density_kth"].items():
+        expected = eval(expr, {"sqrt": math.sqrt})
+        assert abs(r["rho"][idx[c]] - expected) <= 1e-7 * expected
+    order = exact.rank_order(r["key"].astype(np.float64))
+    assert [names[i] for i in order] == golden_example["rank_high_to_low"]
+
+
+def test_example_dependent_points_and_rounds(golden_example):
+    """Fig. 2 dependent points and the Sec. 3.1 rounds for d (L_d = 2, threshold 0)."""
+    X, G, names, idx = example_arrays(golden_example)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=1, k=1)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=golden_example["L_d"],
+                                  threshold=golden_example["threshold"])
+    for c, lam in golden_example["dependent_point"].items():
+        got = dep["lam"][idx[c]]
+        assert (got < 0 and lam is None) or (lam is not None and names[got] == lam), c
+    # round 0 leaves only d (b, the maximum, is skipped); two doubling rounds finish d
+    assert dep["unfinished_round0"] == 1
+    assert dep["rounds"] == 2 and dep["unfinished"] == [1, 0] and dep["tail"] == 0
+    # the candidate sets of those two rounds
+    for rnd in golden_example["dependent_rounds_for_d"]:
+        kd = rnd["k_dep"]
+        ids, _ = oracle.greedy_search(P, G, idx["d"], [idx["d"]], L=kd, k=kd)
+        assert sorted(names[i] for i in ids) == rnd["candidates"]
+    # delta: D(x_i, lambda_i), +inf for the maximum
+    assert math.isinf(dep["delta"][idx["b"]])
+    assert abs(dep["delta"][idx["d"]] - 3.0) < 1e-6
+
+
+def test_example_clusters(golden_example):
+    """Sec. 3 step 5 / Fig. 3: rho_min = 1/sqrt(2) makes e noise; delta_min = 2.5
+    makes b and d centres; clusters {a,b,c}, {d,f}, {e}. The product centre with
+    n_c = 2 picks the same centres."""
+    X, G, names, idx = example_arrays(golden_example)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=1, k=1)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=2, threshold=0)
+    rho_min = np.float32(1.0) / np.sqrt(np.float32(2.0))
+    expected = sorted(sorted(c) for c in golden_example["clusters"])
+    for center, kw in ((oracle.CENTER_THRESHOLD, dict(delta_min=2.5)), (oracle.CENTER_PRODUCT, dict(n_clusters=2))):
+        labels, nc = oracle.cluster(r["rho"], dep["lam"], dep["delta"], center=center, rho_min=rho_min, **kw)
+        groups = {}
+        for i, l in enumerate(labels):
+            groups.setdefault(int(l), []).append(names[i])
+        assert sorted(sorted(g) for g in groups.values()) == expected
+        assert nc == 3
+        # the label of a cluster is its root: b, d and the noise point e
+        assert {names[l] for l in labels} == {"b", "d", "e"}
+
+
+# ---------------------------------------------------------------- distances
+
+def test_canonical_distance_within_fp32_error_bound():
+    """The FP32 canonical squared distance is within the recursive-summation
+    error bound of the exact FP64 value (gamma_m with m = 4d/32 + 5 steps)."""
+    g = np.random.default_rng(5)
+    for d in (4, 32, 128, 1024):
+        X = g.standard_normal((20, d)).astype(np.float32)
+        P = oracle.Points(X)
+        ex = exact.exact_dist_rows(X, np.arange(20)) ** 2
+        m = d // 32 * 4 + 4 + 5 if d >= 128 else 4 + 5
+        gam = m * 2.0 ** -24 / (1 - m * 2.0 ** -24)
+        for a in range(20):
+            for b in range(20):
+                assert abs(oracle.dis(P, a, b) - ex[a, b]) <= gam * ex[a, b] * 1.0001 + 1e-30
+
+
+def test_canonical_distance_u8_is_exact():
+    """uint8 rows: every partial sum is an integer below 2^24, so the FP32
+    result equals the exact integer sum of squared differences."""
+    g = np.random.default_rng(6)
+    X = g.integers(0, 256, size=(16, 128), dtype=np.uint8)
+    P = oracle.Points(X)
+    Xi = X.astype(np.int64)
+    for a in range(16):
+        for b in range(16):
+            assert oracle.dis(P, a, b) == float(((Xi[a] - Xi[b]) ** 2).sum())
+
+
+def test_inner_product_distance():
+    g = np.random.default_rng(7)
+    X = g.standard_normal((10, 64)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    P = oracle.Points(X, metric=oracle.IP)
+    for a in range(10):
+        for b in range(10):
+            ex = 1.0 - float(X[a].astype(np.float64) @ X[b].astype(np.float64))
+            assert abs(oracle.dis(P, a, b) - ex) < 1e-6
+
+
+# ---------------------------------------------------------------- Algorithm 1 special cases
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_full_beam_equals_exact_knn(seed):
+    """With a beam at least n wide on a connected graph, Algorithm 1 visits
+    every point, so it returns the exact k nearest neighbours."""
+    n, d, k = 48, 8, 5
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((n, d)).astype(np.float32)
+    G = random_graph(n, 4, seed)
+    P = oracle.Points(X)
+    ex_ids, ex_d = exact.exact_knn(X, k)
+    for q in range(n):
+        ids, dis = oracle.greedy_search(P, G, q, [q], L=n, k=k)
+        assert len(ids) == k
+        assert np.allclose(np.sqrt(dis), ex_d[q], rtol=1e-5)
+        assert list(ids) == list(ex_ids[q])
+
+
+def test_search_returns_fewer_when_component_is_small():
+    """A query whose component has fewer than k other points gets fewer than k
+    back from Algorithm 1 (the oracle then falls back to brute force, Sec. 4.1)."""
+    X = np.arange(32, dtype=np.float32).reshape(8, 4)
+    G = np.full((8, 2), -1, np.int32)
+    G[0, 0], G[1, 0] = 1, 0  # component {0, 1}
+    for i in range(2, 8):
+        G[i, 0] = 2 + (i - 1) % 6
+    P = oracle.Points(X)
+    ids, _ = oracle.greedy_search(P, G, 0, [0], L=4, k=3)
+    assert list(ids) == [1]
+    r = oracle.knn_density(P, G, L=4, k=3)
+    assert r["fallback"][0] == 1 and r["fallback"][1] == 1
+    ex_ids, _ = exact.exact_knn(X, 3)
+    assert (r["ids"][:2] == ex_ids[:2]).all()
+
+
+def test_pure_python_beam_search_tiny():
+    """Algorithm 1 restated with Python sets on a tiny input, for several
+    beam widths (a second independent statement of the same steps)."""
+    n, d = 30, 4
+    g = np.random.default_rng(11)
+    X = g.integers(-5, 6, size=(n, d)).astype(np.float32)  # integer data: exact, with ties
+    G = random_graph(n, 3, 11)
+    P = oracle.Points(X)
+    D2 = ((X[:, None, :].astype(np.int64) - X[None, :, :].astype(np.int64)) ** 2).sum(-1)
+
+    def key(q, j):
+        return (D2[q, j], j)
+
+    for L in (1, 2, 3, 5, 8):
+        for q in range(n):
+            V = {q}
+            beam = set(int(y) for y in G[q] if y >= 0 and y != q)
+            beam = set(sorted(beam, key=lambda j: key(q, j))[:L])
+            while True:
+                unv = [j for j in beam if j not in V]
+                if not unv:
+                    break
+                p = min(unv, key=lambda j: key(q, j))
+                beam |= set(int(y) for y in G[p] if y >= 0 and y != q)
+                V.add(p)
+                beam = set(sorted(beam, key=lambda j: key(q, j))[:L])
+            res = sorted((beam | V) - {q}, key=lambda j: key(q, j))[:L]
+            ids, _ = oracle.greedy_search(P, G, q, [q], L=L, k=L)
+            assert list(ids) == res, (L, q)
+
+
+# ---------------------------------------------------------------- Algorithm 3 and Definition 2.1
+
+def test_dependent_points_match_definition_with_exact_knn():
+    """With exact k-NN lists (beam >= n) every answer of Algorithm 3 equals
+    Definition 2.1 computed by FP64 brute force from the same ranking."""
+    g = np.random.default_rng(3)
+    n, d, k = 400, 8, 6
+    X = g.standard_normal((n, d)).astype(np.float32)
+    G = random_graph(n, 8, 3)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=n, k=k)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=2 * k, threshold=5)
+    lam, delta = exact.exact_dependent(X, r["key"].astype(np.float64))
+    assert (dep["lam"] == lam).all()
+    fin = np.isfinite(delta)
+    assert np.allclose(dep["delta"][fin], delta[fin], rtol=1e-5)
+
+
+def test_approximate_dependent_distance_is_never_shorter():
+    """Given the same densities, the reported dependent point ranks above the
+    point and is never closer than the exact one (Definition 2.1)."""
+    g = np.random.default_rng(4)
+    n, d, k = 1500, 16, 8
+    X, _ = _mixture(n, d, 8, g)
+    G = random_graph(n, 6, 4)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=16, k=k)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=16, threshold=20)
+    lam_ex, delta_ex = exact.exact_dependent(X, r["key"].astype(np.float64))
+    key = r["key"]
+    has = dep["lam"] >= 0
+    assert (has == (lam_ex >= 0)).all()
+    assert has.sum() == n - 1  # exactly one point, the maximum, has none
+    for i in np.flatnonzero(has):
+        assert ranks_above(key, dep["lam"][i], i)
+    assert (dep["delta"][has] >= delta_ex[has] * (1 - 1e-6)).all()
+
+
+def _mixture(n, d, c, g, box=10.0):
+    centres = g.uniform(-box, box, size=(c, d))
+    lab = g.integers(0, c, size=n)
+    return (centres[lab] + g.standard_normal((n, d))).astype(np.float32), lab
+
+
+# ---------------------------------------------------------------- clusters and ARI
+
+def test_ari_closed_forms():
+    a = np.array([0, 0, 1, 1, 2, 2])
+    assert exact.ari(a, a) == 1.0
+    assert exact.ari(a, a + 7) == 1.0
+    assert exact.ari(np.zeros(5), np.zeros(5)) == 1.0
+    # one pair split: contingency by hand -> ARI = 0.5 * ... computed from the formula terms
+    b = np.array([0, 0, 1, 1, 2, 3])
+    # sum_ij = 2, sum_a = 3, sum_b = 2, total = 15 -> (2 - 6/15) / (2.5 - 6/15) = 1.6 / 2.1
+    assert abs(exact.ari(a, b) - 1.6 / 2.1) < 1e-12
+
+
+def test_ari_matches_sklearn():
+    sk = pytest.importorskip("sklearn.metrics")
+    g = np.random.default_rng(9)
+    for _ in range(5):
+        a = g.integers(0, 5, size=200)
+        b = g.integers(0, 7, size=200)
+        assert abs(exact.ari(a, b) - sk.adjusted_rand_score(a, b)) < 1e-12
+
+
+def test_cluster_root_invariants():
+    """Every label is the root of its tree: a point whose dependent edge was
+    cut, labelled with itself; each non-root point shares its dependent point's label."""
+    g = np.random.default_rng(12)
+    n, d, k = 1000, 8, 6
+    X, _ = _mixture(n, d, 5, g)
+    G = random_graph(n, 6, 12)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=24, k=k)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=24, threshold=10)
+    rho_min = float(np.quantile(r["rho"], 0.05))
+    labels, nc = oracle.cluster(r["rho"], dep["lam"], dep["delta"], center=oracle.CENTER_PRODUCT,
+                                rho_min=rho_min, n_clusters=5)
+    noise = r["rho"] < np.float32(rho_min)
+    roots = np.flatnonzero(labels == np.arange(n))
+    assert len(roots) == nc
+    assert nc == 5 + noise.sum()
+    for i in range(n):
+        if labels[i] != i:
+            assert labels[i] == labels[dep["lam"][i]]
+    # the numpy pointer-jumping restatement gives the same labels
+    lab2, nc2 = exact.cluster(r["rho"], dep["lam"].astype(np.int64), dep["delta"], center="product",
+                              rho_min=np.float32(rho_min), n_clusters=5)
+    assert (lab2 == labels).all() and nc2 == nc
+
+
+def test_well_separated_mixture_ari_one():
+    """Well-separated Gaussians: the same-graph method, on the oracle's own
+    Vamana graph, recovers the generating clusters (ARI = 1) and agrees with
+    exact FP64 DPC."""
+    from paper_2312_03940_gb300 import synth
+    X, lab = synth.gaussian_mixture(n=3000, d=32, components=10, seed=77)
+    P = oracle.Points(X)
+    perm = synth.insertion_order(len(X), seed=78)
+    G = oracle.build_graph(P, R=32, L=64, alpha=1.2, perm=perm, n_start=16)
+    r = oracle.knn_density(P, G, L=64, k=6)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=64, threshold=300)
+    labels, _ = oracle.cluster(r["rho"], dep["lam"], dep["delta"], center=oracle.CENTER_PRODUCT, n_clusters=10)
+    assert exact.ari(labels, lab) == 1.0
+    ex = exact.exact_dpc(X, 6, center="product", n_clusters=10)
+    assert exact.ari(labels, ex["labels"]) == 1.0
+    assert exact.knn_recall(r["dist"], ex["dist"]) >= 0.99
+
+
+# ---------------------------------------------------------------- RobustPrune and the build
+
+def test_robust_prune_characterisation():
+    """The greedy RobustPrune output is the unique list with: (a) ascending
+    (dis, id) order, (b) no kept point dominated by an earlier kept point,
+    (c) every dropped candidate that precedes the last kept one (or any, if
+    fewer than R were kept) dominated by an earlier kept point."""
+    g = np.random.default_rng(13)
+    X = g.standard_normal((300, 16)).astype(np.float32)
+    P = oracle.Points(X)
+    Xd = X.astype(np.float64)
+
+    def d2(a, b):
+        return float(oracle.dis(P, a, b))
+
+    for trial in range(20):
+        p = int(g.integers(300))
+        cand = g.choice(300, size=80, replace=False)
+        alpha, R = (1.0, 1.2, 1.5)[trial % 3], (4, 8, 16, 64)[trial % 4]
+        out = list(oracle.robust_prune(P, p, cand, alpha, R))
+        a2 = np.float32(alpha) * np.float32(alpha)
+        cs = sorted((d2(p, c), c) for c in set(int(c) for c in cand) if c != p)
+        assert out == [c for _, c in sorted((d2(p, c), c) for c in out)]
+        for i, u in enumerate(out):
+            for v in out[:i]:
+                assert not (a2 * np.float32(d2(v, u)) <= np.float32(d2(p, u)))
+        last = (d2(p, out[-1]), out[-1])
+        for dc, c in cs:
+            if c in out:
+                continue
+            if len(out) == R and (dc, c) > last:
+                continue
+            assert any(a2 * np.float32(d2(v, c)) <= np.float32(dc) and (d2(p, v), v) < (dc, c) for v in out)
+    del Xd
+
+
+def test_batch_schedule():
+    """Batches of 1, 2, 4, ... capped at ceil(0.02 n) (Sec. 4.1)."""
+    assert oracle.batch_cap(1_000_000, 0.02) == 20_000
+    assert oracle.batch_cap(10_000, 0.02) == 200
+    assert oracle.batch_cap(30, 0.02) == 1
+
+
+def test_build_graph_invariants_and_recall():
+    from paper_2312_03940_gb300 import synth
+    X, _ = synth.gaussian_mixture(n=2000, d=32, components=10, seed=31)
+    P = oracle.Points(X)
+    R = 32
+    perm = synth.insertion_order(len(X), seed=32)
+    G = oracle.build_graph(P, R=R, L=64, alpha=1.2, perm=perm, n_start=16)
+    n = len(X)
+    for i in range(n):
+        row = G[i]
+        deg = int((row >= 0).sum())
+        assert (row[:deg] >= 0).all() and (row[deg:] == -1).all()
+        assert i not in row[:deg]
+        assert len(set(row[:deg].tolist())) == deg
+    # (almost) every point is reachable from the start points: Vamana does not
+    # guarantee it, a point whose in-edges were all pruned stays unreachable
+    seen = set(perm[:16].tolist())
+    stack = list(seen)
+    while stack:
+        u = stack.pop()
+        for v in G[u]:
+            if v >= 0 and v not in seen:
+                seen.add(int(v))
+                stack.append(int(v))
+    assert len(seen) >= 0.995 * n
+    r = oracle.knn_density(P, G, L=64, k=10)
+    _, ex_d = exact.exact_knn(X, 10)
+    assert exact.knn_recall(r["dist"], ex_d) >= 0.95
+
+
+def test_build_graph_deterministic_across_threads():
+    from paper_2312_03940_gb300 import synth
+    X, _ = synth.gaussian_mixture(n=1500, d=16, components=5, seed=41)
+    P = oracle.Points(X)
+    perm = synth.insertion_order(len(X), seed=42)
+    G1 = oracle.build_graph(P, R=12, L=24, alpha=1.2, perm=perm, n_start=4, threads=1)
+    G8 = oracle.build_graph(P, R=12, L=24, alpha=1.2, perm=perm, n_start=4, threads=8)
+    assert (G1 == G8).all()
+
+
+# ---------------------------------------------------------------- exact oracle vs pure Python
+
+def test_exact_oracle_against_python_loops():
+    """exact.exact_knn / exact_dependent against a direct double loop on a tiny input."""
+    g = np.random.default_rng(21)
+    n, d, k = 25, 3, 4
+    X = g.standard_normal((n, d)).astype(np.float32)
+    ids, dist = exact.exact_knn(X, k)
+    rho, key = exact.density(dist, "kth")
+    lam, delta = exact.exact_dependent(X, key)
+    for i in range(n):
+        ds = []
+        for j in range(n):
+            if j != i:
+                ds.append((math.sqrt(sum((float(X[i, t]) - float(X[j, t])) ** 2 for t in range(d))), j))
+        ds.sort()
+        assert [j for _, j in ds[:k]] == list(ids[i])
+        assert abs(1.0 / ds[k - 1][0] - rho[i]) < 1e-12 * rho[i]
+        higher = [(dd, j) for dd, j in ds if ranks_above(key, j, i)]
+        if higher:
+            assert lam[i] == min(higher)[1]
+        else:
+            assert lam[i] == -1
