@@ -1,0 +1,233 @@
+/*
+ * pecann.h -- C ABI of the GB300 density-peaks-clustering library.
+ *
+ * The library runs the data-parallel path of PECANN's density peaks
+ * clustering (DPC) on one GPU: batched greedy beam search (Algorithm 1) over a
+ * fixed-degree Vamana graph, used to build the graph (Sec. 3.2), to find each
+ * point's k nearest neighbours and density (Algorithm 2 lines 2-4, Sec. 4.2),
+ * and to find dependent points with doubling beam-width rounds (Algorithm 3);
+ * then noise / center / union-find cut the dependent forest into clusters
+ * (Algorithm 2 lines 5-7).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* and every array argument not marked "host" are DEVICE
+ *    pointers. The caller owns all memory; the library never allocates,
+ *    frees or keeps a pointer after the call returns.
+ *  - `ws` is a caller-provided device workspace of `ws_bytes` bytes, 256-byte
+ *    aligned, of at least pecann_workspace_size() bytes. Its contents on entry
+ *    do not matter; on return they are undefined.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *    queued on it. pecann_search, pecann_build_graph and
+ *    pecann_dependent_points return only after their work on `stream` has
+ *    finished (they read back an error word or small counters); the other
+ *    calls are asynchronous unless a host output is requested.
+ *  - Errors are returned as pecann_status; nothing is thrown across the ABI.
+ *    PECANN_EINVAL: an argument is out of range (checked on the host before
+ *    any GPU work); PECANN_ENOMEM: ws_bytes is too small; PECANN_ECUDA: a
+ *    CUDA call failed (the message is available from pecann_last_error());
+ *    PECANN_EUNSUPPORTED: a valid combination this build has no kernel for;
+ *    PECANN_EINTERNAL: a kernel detected an inconsistency (e.g. a graph entry
+ *    out of range) and skipped the offending access.
+ *  - Point rows are n x d, row-major, contiguous, 16-byte aligned. d must be
+ *    a multiple of 4 (FP32), 8 (BF16) or 16 (U8, FP8). U8 supports the L2
+ *    metric with d <= 256 (so that every distance is an exact integer in FP32).
+ *  - Distances: the library orders points by the FP32 "dissimilarity" dis --
+ *    the squared Euclidean distance (L2) or 1 - <x, y> (IP, unit-norm rows) --
+ *    summed in one fixed order: 4-element chunk c of a row is accumulated with
+ *    fmaf into partial c mod 32, chunks in ascending order, then the 32
+ *    partials are combined by an xor butterfly (offsets 16, 8, 4, 2, 1).
+ *    Reported distances D are sqrt(dis) for L2 and dis for IP. Ties are
+ *    broken by the smaller id everywhere.
+ *  - Graphs are n x R int32 out-neighbour lists, -1 padded; all ids < n.
+ */
+#ifndef PECANN_H
+#define PECANN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PECANN_API __attribute__((visibility("default")))
+#else
+#define PECANN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PECANN_OK = 0,
+  PECANN_EINVAL = 1,
+  PECANN_ENOMEM = 2,
+  PECANN_ECUDA = 3,
+  PECANN_ETIMEOUT = 4,
+  PECANN_EUNSUPPORTED = 5,
+  PECANN_EINTERNAL = 6
+} pecann_status;
+
+typedef enum { PECANN_F32 = 0, PECANN_U8 = 1, PECANN_BF16 = 2, PECANN_FP8E4M3 = 3 } pecann_dtype;
+typedef enum { PECANN_L2 = 0, PECANN_IP = 1 } pecann_metric;
+
+/* Density functions (Sec. 4.2 and Appendix A). */
+typedef enum {
+  PECANN_DENS_KTH = 0,    /* rho = 1 / D(x_i, k-th neighbour)            */
+  PECANN_DENS_EXPSUM = 1, /* rho = exp(-sum_j D^2 / k); ranked by exponent */
+  PECANN_DENS_SUMEXP = 2, /* rho = sum_j exp(-D^2) / k                    */
+  PECANN_DENS_SUM = 3     /* rho = -sum_j D                               */
+} pecann_density_fn;
+
+/* Center functions (Sec. 4.2). */
+typedef enum {
+  PECANN_CENTER_THRESHOLD = 0, /* delta_i > delta_min                   */
+  PECANN_CENTER_PRODUCT = 1    /* the n_clusters largest delta_i * rho_i  */
+} pecann_center_fn;
+
+/* Parameters of the method. pecann_params_default() fills the paper's
+   defaults; every field is read by the calls named beside it. */
+typedef struct {
+  int32_t k;                 /* neighbours per point (density)            density, dependent */
+  int32_t R;                 /* graph degree bound                         all graph calls    */
+  int32_t L_build;           /* beam width of the build searches           build              */
+  int32_t L_search;          /* beam width of the k-NN searches            density            */
+  int32_t L_dep;             /* initial k_dep of the doubling rounds (L_d) dependent          */
+  float alpha;               /* RobustPrune slack, >= 1                    build              */
+  int32_t n_start;           /* sampled start points, 1..min(n, L_build)  build              */
+  float batch_frac;          /* batch size cap as a fraction of n (0.02)   build              */
+  int32_t visit_cap;         /* closest visited points kept per build search (0: 2*L_build)   */
+  int32_t dep_threshold;     /* doubling continues while > this many are unfinished (300)     */
+  int32_t max_dep_rounds;    /* cap on doubling rounds                     dependent          */
+  int32_t max_dep_beam;      /* largest k_dep searched on the graph (<= 8192) dependent       */
+  int32_t density;           /* pecann_density_fn                          density            */
+  int32_t normalize_density; /* rho'_i = rho_i k / sum_{j in N_i} rho_j    density            */
+  int32_t center;            /* pecann_center_fn                           cluster            */
+  float rho_min;             /* noise: rho_i < rho_min                     cluster            */
+  float delta_min;           /* threshold center                          cluster            */
+  int32_t n_clusters;        /* product center                            cluster            */
+  int32_t hash_slots;        /* per-query seen-filter slots (power of 2; 0 = automatic)      */
+  int32_t reserved0;
+  uint64_t seed;             /* insertion order when none is given         build              */
+} pecann_params;
+
+/* A point set. */
+typedef struct {
+  const void* data;       /* device, n x d row-major rows of `dtype`            */
+  int64_t n;              /* number of points, 2 <= n < 2^31                     */
+  int32_t d;              /* dimensions                                          */
+  int32_t dtype;          /* pecann_dtype                                        */
+  int32_t metric;         /* pecann_metric                                       */
+  int32_t reserved0;
+  const float* dim_scale; /* FP8 only: device, d per-dimension scales (x = q * s) */
+  const float* data_f32;  /* BF16/FP8 only: device n x d FP32 rows for the exact
+                             re-rank; NULL for FP32/U8 data                      */
+} pecann_dataset;
+
+/* Fills the defaults: k 16, R 32, L_build 64, L_search 64, L_dep 64,
+   alpha 1.1, n_start 16, batch_frac 0.02, visit_cap 0, dep_threshold 300,
+   max_dep_rounds 30, max_dep_beam 8192, kth density, no normalisation,
+   product center, rho_min 0, delta_min 0, n_clusters 1, seed 0. */
+PECANN_API void pecann_params_default(pecann_params* p);
+
+/* Static string for a status code. */
+PECANN_API const char* pecann_status_string(int status);
+
+/* Text of the last CUDA or validation error seen by this thread ("" if none). */
+PECANN_API const char* pecann_last_error(void);
+
+/* Library version, as major*10000 + minor*100 + patch. */
+PECANN_API int32_t pecann_version(void);
+
+/* Workspace bytes that are enough for every call below on this dataset and
+   these parameters (host call; no GPU work). */
+PECANN_API pecann_status pecann_workspace_size(const pecann_dataset* ds, const pecann_params* p, size_t* bytes);
+
+/*
+ * Greedy beam search, Algorithm 1, for m query points of the dataset.
+ * Query q = d_queries[i] starts from the set {q} (its out-neighbours are the
+ * first candidates) when d_start is NULL, else from the n_start ids of
+ * d_start; the query itself never enters the beam and is never returned.
+ * Beam width L (1 <= L <= 8192), result size k (1 <= k <= L).
+ * Output per query i: d_ids[i*k .. i*k+k) and d_dis[...] -- the min(k, |beam|)
+ * closest points found, ascending by (dis, id), -1 / +inf padded -- and
+ * d_count[i] = number of valid entries. dis is the ordering value.
+ */
+PECANN_API pecann_status pecann_search(const pecann_dataset* ds, const int32_t* d_graph, int32_t R,
+                            const int32_t* d_queries, int64_t m, const int32_t* d_start,
+                            int32_t n_start, int32_t L, int32_t k, int32_t* d_ids, float* d_dis,
+                            int32_t* d_count, const pecann_params* p, void* ws, size_t ws_bytes,
+                            void* stream);
+
+/*
+ * Vamana graph construction by batched insertion (Sec. 3.2, Sec. 4.1).
+ * Points are inserted in the order d_order (device, a permutation of
+ * 0..n-1), or, if d_order is NULL, in a permutation drawn from p->seed. The
+ * first p->n_start points of the order are the start points of every build
+ * search. Batches hold 1, 2, 4, ... points, capped at ceil(batch_frac * n);
+ * every search of a batch sees the graph as it stood at the batch start. Each
+ * inserted point p gets RobustPrune(p, V_p u N_out(p), alpha, R) where V_p are
+ * the visit_cap closest points its search visited; then each new edge p -> y
+ * adds p to y, re-pruning y when its degree would exceed R.
+ * Output: d_graph (n x R int32, -1 padded) and, if not NULL, d_degree (n).
+ * Blocks until done.
+ */
+PECANN_API pecann_status pecann_build_graph(const pecann_dataset* ds, const pecann_params* p,
+                                 const int32_t* d_order, int32_t* d_graph, int32_t* d_degree,
+                                 void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * k nearest neighbours and density of every point (Algorithm 2 lines 2-4).
+ * N_i = the k closest points returned by Algorithm 1 for x_i with start set
+ * {x_i} and beam width L_search; where the search returns fewer than k points
+ * N_i is computed exactly by brute force (Sec. 4.1).
+ * Outputs: d_knn_ids (n x k int32) and d_knn_dist (n x k float, reported
+ * distances D), ascending by (dis, id); d_density (n, rho); d_rank_key (n):
+ * the value points are ranked by -- rho, or the exponent -sum(D^2)/k for the
+ * exp-sum density. Point j ranks above i iff key_j > key_i, or the keys are
+ * equal and j < i (Sec. 3: ties broken by id).
+ */
+PECANN_API pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph,
+                             const pecann_params* p, int32_t* d_knn_ids, float* d_knn_dist,
+                             float* d_density, float* d_rank_key, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/*
+ * Dependent points, Algorithm 3 (ComputeDepPts). d_rank_key, d_knn_ids and
+ * d_knn_dist are the outputs of pecann_density. Round 0: lambda_i = the
+ * first point of N_i ranked above x_i. Then, while more than dep_threshold
+ * points are unfinished (the maximum-rank point excluded), each unfinished
+ * point runs Algorithm 1 with beam width and result size k_dep (L_dep,
+ * doubling every round) and takes the closest returned point ranked above it.
+ * Doubling stops after max_dep_rounds rounds or when k_dep would exceed
+ * max_dep_beam; the rest is finished exactly by brute force over all points.
+ * Outputs: d_dep (n, -1 for the maximum-rank point) and d_dep_dist (n, D to
+ * the dependent point, +inf where there is none). If h_stats (HOST, 64
+ * int64) is not NULL: [0] rounds run, [1] unfinished after round 0, [2+r]
+ * unfinished after round r, [63] points finished by brute force.
+ * Blocks until done.
+ */
+PECANN_API pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d_graph,
+                                      const pecann_params* p, const float* d_rank_key,
+                                      const int32_t* d_knn_ids, const float* d_knn_dist,
+                                      int32_t* d_dep, float* d_dep_dist, int64_t* h_stats,
+                                      void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Clusters (Algorithm 2 lines 5-7). Noise: rho_i < rho_min. Centers among the
+ * other points: delta_i > delta_min (threshold) or the n_clusters largest
+ * delta_i * rho_i (product; ties by smaller id, 0 * inf taken as 0). Every
+ * point that is neither noise nor a center and has a dependent point joins
+ * its dependent point's cluster (union-find); d_labels[i] = the id of the
+ * root of i's tree in the cut dependent forest, i.e. the cluster's center,
+ * the noise point itself, or the maximum-rank point.
+ * If h_n_clusters (HOST) is not NULL it receives the number of clusters
+ * (the call then waits for the stream).
+ */
+PECANN_API pecann_status pecann_cluster(int64_t n, const float* d_density, const int32_t* d_dep,
+                             const float* d_dep_dist, const pecann_params* p, int32_t* d_labels,
+                             int64_t* h_n_clusters, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PECANN_H */

@@ -1,0 +1,438 @@
+// The C ABI (include/pecann.h): argument checks, workspace layout, and the
+// host loops that sequence the kernels.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pecann {
+
+cudaError_t run_cluster(int64_t n, const float* rho, const int32_t* lam, const float* delta, int center_fn,
+                        float rho_min, float delta_min, int32_t n_clusters, int32_t* labels, void* ws,
+                        unsigned long long* d_roots, cudaStream_t st);
+size_t cluster_ws_bytes(int64_t n);
+size_t build_ws_bytes(int64_t n, const pecann_params& p, int64_t cap, int vcap);
+int64_t batch_cap_of(int64_t n, float frac);
+cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t* d_order, int32_t* G,
+                      int32_t* d_degree, void* ws, int* d_err, int log2h, cudaStream_t st);
+
+__global__ void k_dep_round0(int64_t n, int k, const int32_t* knn_ids, const float* knn_dist, const float* rk,
+                             int32_t* lam, float* delta);
+__global__ void k_rank_max(int64_t n, const float* rk, unsigned long long* out);
+__global__ void k_compact_unfinished(const int32_t* src, int64_t m, const int32_t* lam,
+                                     const unsigned long long* gmax, int32_t* dst, int32_t* cnt);
+__global__ void k_normalize_density(int64_t n, int k, const int32_t* knn_ids, const float* raw, float* rho,
+                                    float* rk);
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Header of every workspace: an error word and small counters.
+struct WsHeader {
+  int err;
+  int pad0;
+  int32_t counts[14];
+  unsigned long long gmax;
+  unsigned long long roots;
+};
+static const size_t HDR = 256;
+
+static int elem_bytes(int dtype) { return dtype == DT_F32 ? 4 : (dtype == DT_BF16 ? 2 : 1); }
+
+static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv) {
+  if (!ds || !ds->data) return set_last_error("dataset or data pointer is NULL"), PECANN_EINVAL;
+  if (ds->n < 2 || ds->n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
+  if (ds->dtype < 0 || ds->dtype > 3 || ds->metric < 0 || ds->metric > 1)
+    return set_last_error("bad dtype or metric"), PECANN_EINVAL;
+  int epc = 16 / elem_bytes(ds->dtype);
+  if (ds->d <= 0 || ds->d % epc) return set_last_error("d must be a positive multiple of 16 bytes / element size"), PECANN_EINVAL;
+  if (((uintptr_t)ds->data) & 15) return set_last_error("rows must be 16-byte aligned"), PECANN_EINVAL;
+  Layout L;
+  if (!pick_layout(ds->dtype, ds->metric, ds->d, &L))
+    return set_last_error("no kernel for this dtype / metric / d"), PECANN_EUNSUPPORTED;
+  dv->X = (const uint8_t*)ds->data;
+  dv->n = ds->n;
+  dv->d = ds->d;
+  dv->dtype = ds->dtype;
+  dv->metric = ds->metric;
+  dv->row_bytes = (int64_t)ds->d * elem_bytes(ds->dtype);
+  dv->C = (int)(dv->row_bytes / 16);
+  return PECANN_OK;
+}
+
+static int log2_hash(const pecann_params* p, int Lw) {
+  int slots = p->hash_slots;
+  if (slots <= 0) {
+    slots = 16 * Lw;
+    slots = std::max(2048, std::min(slots, 16384));
+  }
+  int l = 0;
+  while ((1 << l) < slots) l++;
+  return std::max(4, std::min(l, 16));
+}
+
+static pecann_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PECANN_OK;
+  if (e == cudaErrorNotSupported) {
+    set_last_error(std::string(what) + ": unsupported combination");
+    return PECANN_EUNSUPPORTED;
+  }
+  set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return PECANN_ECUDA;
+}
+
+static pecann_status read_err(int* d_err, cudaStream_t st) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "error readback");
+  if (h) {
+    set_last_error(h == ERR_BAD_ID ? "graph or query id out of range"
+                                   : (h == ERR_NO_PROGRESS ? "search made no progress" : "capacity exceeded"));
+    return PECANN_EINTERNAL;
+  }
+  return PECANN_OK;
+}
+
+static pecann_status check_params(const pecann_params* p, int64_t n) {
+  if (!p) return set_last_error("params is NULL"), PECANN_EINVAL;
+  if (p->R < 1 || p->R > 256) return set_last_error("R must be in 1..256"), PECANN_EINVAL;
+  if (p->k < 1 || p->k >= n || p->k > 1024) return set_last_error("k must be in 1..min(n-1, 1024)"), PECANN_EINVAL;
+  if (p->L_search < p->k || p->L_search > 8192) return set_last_error("L_search must be in k..8192"), PECANN_EINVAL;
+  if (p->hash_slots < 0 || (p->hash_slots & (p->hash_slots - 1)))
+    return set_last_error("hash_slots must be 0 or a power of 2"), PECANN_EINVAL;
+  return PECANN_OK;
+}
+
+// Workspace pieces of each call (bytes after the header).
+static size_t density_bytes(int64_t n) { return 2 * al((size_t)n * 4); }
+static size_t dep_bytes(int64_t n) { return 2 * al((size_t)n * 4) + al((size_t)n * 8); }
+
+}  // namespace pecann
+
+using namespace pecann;
+
+extern "C" {
+
+void pecann_params_default(pecann_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->k = 16;
+  p->R = 32;
+  p->L_build = 64;
+  p->L_search = 64;
+  p->L_dep = 64;
+  p->alpha = 1.1f;
+  p->n_start = 16;
+  p->batch_frac = 0.02f;
+  p->visit_cap = 0;
+  p->dep_threshold = 300;
+  p->max_dep_rounds = 30;
+  p->max_dep_beam = 8192;
+  p->density = PECANN_DENS_KTH;
+  p->normalize_density = 0;
+  p->center = PECANN_CENTER_PRODUCT;
+  p->rho_min = 0.0f;
+  p->delta_min = 0.0f;
+  p->n_clusters = 1;
+  p->hash_slots = 0;
+  p->seed = 0;
+}
+
+const char* pecann_status_string(int s) {
+  switch (s) {
+    case PECANN_OK: return "ok";
+    case PECANN_EINVAL: return "invalid argument";
+    case PECANN_ENOMEM: return "workspace too small";
+    case PECANN_ECUDA: return "CUDA error";
+    case PECANN_ETIMEOUT: return "device wait timed out";
+    case PECANN_EUNSUPPORTED: return "unsupported";
+    case PECANN_EINTERNAL: return "kernel-detected inconsistency";
+    default: return "unknown status";
+  }
+}
+
+const char* pecann_last_error(void) { return g_last_error.c_str(); }
+
+int32_t pecann_version(void) { return 100; }
+
+pecann_status pecann_workspace_size(const pecann_dataset* ds, const pecann_params* p, size_t* bytes) {
+  if (!ds || !p || !bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
+  int64_t n = ds->n;
+  if (n < 2) return set_last_error("n out of range"), PECANN_EINVAL;
+  size_t b = density_bytes(n);
+  b = std::max(b, dep_bytes(n));
+  b = std::max(b, cluster_ws_bytes(n));
+  if (p->R >= 1 && p->L_build >= 1) {
+    int vcap = p->visit_cap > 0 ? p->visit_cap : 2 * p->L_build;
+    b = std::max(b, build_ws_bytes(n, *p, batch_cap_of(n, p->batch_frac > 0 ? p->batch_frac : 0.02f), vcap));
+  }
+  *bytes = HDR + b + 4096;
+  return PECANN_OK;
+}
+
+pecann_status pecann_search(const pecann_dataset* ds, const int32_t* d_graph, int32_t R,
+                            const int32_t* d_queries, int64_t m, const int32_t* d_start, int32_t n_start,
+                            int32_t L, int32_t k, int32_t* d_ids, float* d_dis, int32_t* d_count,
+                            const pecann_params* p, void* ws, size_t ws_bytes, void* stream) {
+  DataView dv;
+  pecann_status s = check_dataset(ds, &dv);
+  if (s) return s;
+  if (!d_graph || !d_ids || !d_dis || !d_count || !ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if (R < 1 || R > 256 || L < 1 || L > 8192 || k < 1 || k > L || m < 0)
+    return set_last_error("R, L, k or m out of range"), PECANN_EINVAL;
+  if (d_start && (n_start < 1 || n_start > 1024)) return set_last_error("n_start out of range"), PECANN_EINVAL;
+  if (ws_bytes < HDR) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  pecann_params dp;
+  pecann_params_default(&dp);
+  if (!p) p = &dp;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* h = (WsHeader*)ws;
+  cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  SearchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.X = dv.X;
+  a.row_bytes = dv.row_bytes;
+  a.n = dv.n;
+  a.C = dv.C;
+  a.G = d_graph;
+  a.R = R;
+  a.queries = d_queries;
+  a.nq = m;
+  a.S = d_start;
+  a.nS = d_start ? n_start : 0;
+  a.Lw = L;
+  a.log2h = log2_hash(p, L);
+  a.stage = (std::max(R, a.nS) + 31) & ~31;
+  a.mode = MODE_RAW;
+  a.metric = dv.metric;
+  a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
+  a.k = k;
+  a.out_ids = d_ids;
+  a.out_dis = d_dis;
+  a.out_cnt = d_count;
+  a.err = &h->err;
+  if ((s = cuda_status(launch_search(dv, a, st), "search"))) return s;
+  return read_err(&h->err, st);
+}
+
+pecann_status pecann_build_graph(const pecann_dataset* ds, const pecann_params* p, const int32_t* d_order,
+                                 int32_t* d_graph, int32_t* d_degree, void* ws, size_t ws_bytes, void* stream) {
+  DataView dv;
+  pecann_status s = check_dataset(ds, &dv);
+  if (s) return s;
+  if (!p || !d_graph || !ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if (p->R < 1 || p->R > 256) return set_last_error("R must be in 1..256"), PECANN_EINVAL;
+  if (p->L_build < 1 || p->L_build > 1024) return set_last_error("L_build must be in 1..1024"), PECANN_EINVAL;
+  if (!(p->alpha >= 1.0f)) return set_last_error("alpha must be >= 1"), PECANN_EINVAL;
+  if (p->n_start < 1 || p->n_start > dv.n || p->n_start > p->L_build || p->n_start > 1024)
+    return set_last_error("n_start must be in 1..min(n, L_build)"), PECANN_EINVAL;
+  if (!(p->batch_frac > 0.0f) || p->batch_frac > 1.0f) return set_last_error("batch_frac must be in (0, 1]"), PECANN_EINVAL;
+  int vcap = p->visit_cap > 0 ? p->visit_cap : 2 * p->L_build;
+  if (vcap + p->R > 4096) return set_last_error("visit_cap + R must be <= 4096"), PECANN_EINVAL;
+  if (p->hash_slots < 0 || (p->hash_slots & (p->hash_slots - 1)))
+    return set_last_error("hash_slots must be 0 or a power of 2"), PECANN_EINVAL;
+  size_t need = HDR + build_ws_bytes(dv.n, *p, batch_cap_of(dv.n, p->batch_frac), vcap);
+  if (ws_bytes < need) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* h = (WsHeader*)ws;
+  cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  e = run_build(dv, *p, d_order, d_graph, d_degree, (uint8_t*)ws + HDR, &h->err, log2_hash(p, p->L_build), st);
+  if ((s = cuda_status(e, "build"))) return s;
+  return read_err(&h->err, st);
+}
+
+pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, const pecann_params* p,
+                             int32_t* d_knn_ids, float* d_knn_dist, float* d_density, float* d_rank_key,
+                             void* ws, size_t ws_bytes, void* stream) {
+  DataView dv;
+  pecann_status s = check_dataset(ds, &dv);
+  if (s) return s;
+  if ((s = check_params(p, dv.n))) return s;
+  if (!d_graph || !d_knn_ids || !d_knn_dist || !d_density || !d_rank_key || !ws)
+    return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if (p->density < 0 || p->density > 3) return set_last_error("bad density function"), PECANN_EINVAL;
+  if (ws_bytes < HDR + density_bytes(dv.n)) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* h = (WsHeader*)ws;
+  uint8_t* w = (uint8_t*)ws + HDR;
+  int32_t* fb_list = (int32_t*)w;
+  float* raw = (float*)(w + al((size_t)dv.n * 4));
+  cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  SearchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.X = dv.X;
+  a.row_bytes = dv.row_bytes;
+  a.n = dv.n;
+  a.C = dv.C;
+  a.G = d_graph;
+  a.R = p->R;
+  a.queries = nullptr;
+  a.nq = dv.n;
+  a.Lw = p->L_search;
+  a.log2h = log2_hash(p, a.Lw);
+  a.stage = (p->R + 31) & ~31;
+  a.mode = MODE_KNN;
+  a.metric = dv.metric;
+  a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
+  a.k = p->k;
+  a.out_ids = d_knn_ids;
+  a.out_dis = d_knn_dist;
+  a.rho = d_density;
+  a.rkey = d_rank_key;
+  a.density_fn = p->density;
+  a.fb_list = fb_list;
+  a.fb_cnt = &h->counts[0];
+  a.err = &h->err;
+  if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
+  // points whose search returned fewer than k: exact k-NN by brute force
+  e = launch_bruteforce_knn(dv, fb_list, &h->counts[0], dv.n, p->k, d_knn_ids, d_knn_dist, d_density,
+                            d_rank_key, p->density, &h->err, st);
+  if ((s = cuda_status(e, "brute-force k-NN"))) return s;
+  if (p->normalize_density) {
+    if ((e = cudaMemcpyAsync(raw, d_density, (size_t)dv.n * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return cuda_status(e, "copy");
+    unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
+    k_normalize_density<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, raw, d_density, d_rank_key);
+    if ((s = cuda_status(cudaGetLastError(), "normalize"))) return s;
+  }
+  return PECANN_OK;
+}
+
+pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d_graph, const pecann_params* p,
+                                      const float* d_rank_key, const int32_t* d_knn_ids, const float* d_knn_dist,
+                                      int32_t* d_dep, float* d_dep_dist, int64_t* h_stats, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  DataView dv;
+  pecann_status s = check_dataset(ds, &dv);
+  if (s) return s;
+  if ((s = check_params(p, dv.n))) return s;
+  if (!d_graph || !d_rank_key || !d_knn_ids || !d_knn_dist || !d_dep || !d_dep_dist || !ws)
+    return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if (p->L_dep < 1 || p->max_dep_beam < 1 || p->max_dep_beam > 8192 || p->dep_threshold < 0 ||
+      p->max_dep_rounds < 0)
+    return set_last_error("L_dep, max_dep_beam (<= 8192), dep_threshold or max_dep_rounds out of range"),
+           PECANN_EINVAL;
+  if (ws_bytes < HDR + dep_bytes(dv.n)) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* h = (WsHeader*)ws;
+  uint8_t* w = (uint8_t*)ws + HDR;
+  int32_t* U0 = (int32_t*)w;
+  int32_t* U1 = (int32_t*)(w + al((size_t)dv.n * 4));
+  unsigned long long* best = (unsigned long long*)(w + 2 * al((size_t)dv.n * 4));
+  int64_t stats[64];
+  memset(stats, 0, sizeof(stats));
+  cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  const unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
+  // the maximum-rank point has no dependent point
+  k_rank_max<<<blocks, 256, 0, st>>>(dv.n, d_rank_key, &h->gmax);
+  // round 0: lambda_i <- DPBruteForce(x_i, N_i)
+  k_dep_round0<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, d_knn_dist, d_rank_key, d_dep, d_dep_dist);
+  // P_unfinished, the maximum skipped
+  k_compact_unfinished<<<blocks, 256, 0, st>>>(nullptr, dv.n, d_dep, &h->gmax, U0, &h->counts[1]);
+  if ((s = cuda_status(cudaGetLastError(), "round 0"))) return s;
+  int32_t nu = 0;
+  if ((e = cudaMemcpyAsync(&nu, &h->counts[1], 4, cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+    e = cudaStreamSynchronize(st);
+  if ((s = cuda_status(e, "readback"))) return s;
+  stats[1] = nu;
+  int64_t kdep = p->L_dep;
+  int rounds = 0;
+  while (nu > p->dep_threshold && rounds < p->max_dep_rounds && kdep <= p->max_dep_beam) {
+    SearchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.X = dv.X;
+    a.row_bytes = dv.row_bytes;
+    a.n = dv.n;
+    a.C = dv.C;
+    a.G = d_graph;
+    a.R = p->R;
+    a.queries = U0;
+    a.nq = nu;
+    a.Lw = (int)kdep;
+    a.log2h = log2_hash(p, a.Lw);
+    a.stage = (p->R + 31) & ~31;
+    a.mode = MODE_DEP;
+    a.metric = dv.metric;
+    a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
+    a.rank_key = d_rank_key;
+    a.lam = d_dep;
+    a.delta = d_dep_dist;
+    a.err = &h->err;
+    // N_candidates <- FindKnn(i, k_dep); lambda_i <- DPBruteForce(x_i, N_candidates)
+    if ((s = cuda_status(launch_search(dv, a, st), "dependent search"))) return s;
+    if ((e = cudaMemsetAsync(&h->counts[2], 0, 4, st)) != cudaSuccess) return cuda_status(e, "memset");
+    unsigned ub = (unsigned)std::min<int64_t>((nu + 255) / 256, (int64_t)num_sms() * 8);
+    k_compact_unfinished<<<ub, 256, 0, st>>>(U0, nu, d_dep, &h->gmax, U1, &h->counts[2]);
+    if ((s = cuda_status(cudaGetLastError(), "compact"))) return s;
+    if ((e = cudaMemcpyAsync(&nu, &h->counts[2], 4, cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+      e = cudaStreamSynchronize(st);
+    if ((s = cuda_status(e, "readback"))) return s;
+    std::swap(U0, U1);
+    kdep *= 2;
+    if (rounds < 60) stats[2 + rounds] = nu;
+    rounds++;
+  }
+  stats[0] = rounds;
+  stats[63] = nu;
+  // the rest: DPBruteForce over all of P
+  e = launch_dep_bruteforce(dv, U0, nu, d_rank_key, best, d_dep, d_dep_dist, st);
+  if ((s = cuda_status(e, "brute-force tail"))) return s;
+  if ((s = read_err(&h->err, st))) return s;
+  if (h_stats) memcpy(h_stats, stats, sizeof(stats));
+  return PECANN_OK;
+}
+
+pecann_status pecann_cluster(int64_t n, const float* d_density, const int32_t* d_dep, const float* d_dep_dist,
+                             const pecann_params* p, int32_t* d_labels, int64_t* h_n_clusters, void* ws,
+                             size_t ws_bytes, void* stream) {
+  if (!p || !d_density || !d_dep || !d_dep_dist || !d_labels || !ws)
+    return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if (n < 1 || n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
+  if (p->center != PECANN_CENTER_THRESHOLD && p->center != PECANN_CENTER_PRODUCT)
+    return set_last_error("bad center function"), PECANN_EINVAL;
+  if (p->center == PECANN_CENTER_PRODUCT && p->n_clusters < 1)
+    return set_last_error("n_clusters must be >= 1"), PECANN_EINVAL;
+  if (ws_bytes < HDR + cluster_ws_bytes(n)) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* h = (WsHeader*)ws;
+  cudaError_t e = run_cluster(n, d_density, d_dep, d_dep_dist, p->center, p->rho_min, p->delta_min, p->n_clusters,
+                              d_labels, (uint8_t*)ws + HDR, h_n_clusters ? &h->roots : nullptr, st);
+  pecann_status s = cuda_status(e, "cluster");
+  if (s) return s;
+  if (h_n_clusters) {
+    unsigned long long r = 0;
+    e = cudaMemcpyAsync(&r, &h->roots, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if ((s = cuda_status(e, "readback"))) return s;
+    *h_n_clusters = (int64_t)r;
+  }
+  return PECANN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Dependent points (Algorithm 3) outside the beam search itself: round 0
+// over the k-NN lists, the global maximum, compaction of the unfinished
+// points, the exact brute-force tail, and the normalised density pass.
+#include "common.cuh"
+#include "internal.h"
+
+namespace pecann {
+
+// Rank key of a point as one integer: larger = ranked higher (key
+// descending, then id ascending).
+__device__ __forceinline__ unsigned long long rank64(const float* rk, int32_t i) {
+  return ((unsigned long long)f2ord(__ldg(rk + i)) << 32) | (0xffffffffu - (uint32_t)i);
+}
+
+// Round 0: lambda_i <- DPBruteForce(x_i, N_i), N_i sorted by (dis, id), so
+// the first point of N_i ranked above x_i is the closest one.
+__global__ void k_dep_round0(int64_t n, int k, const int32_t* knn_ids, const float* knn_dist,
+                             const float* rk, int32_t* lam, float* delta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t best = -1;
+    float bd = INFINITY;
+    for (int t = 0; t < k; t++) {
+      int32_t j = knn_ids[i * k + t];
+      if (j >= 0 && ranks_above(rk, j, (int32_t)i)) {
+        best = j;
+        bd = knn_dist[i * k + t];
+        break;
+      }
+    }
+    lam[i] = best;
+    delta[i] = bd;
+  }
+}
+
+// The point of maximum rank (it has no dependent point).
+__global__ void k_rank_max(int64_t n, const float* rk, unsigned long long* out) {
+  unsigned long long best = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long v = rank64(rk, (int32_t)i);
+    best = v > best ? v : best;
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    unsigned long long o = __shfl_xor_sync(FULL, best, off);
+    best = o > best ? o : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+// P_unfinished <- par-filter(src, lambda_i = none), the maximum excluded.
+// src == NULL means all points 0..m-1.
+__global__ void k_compact_unfinished(const int32_t* src, int64_t m, const int32_t* lam,
+                                     const unsigned long long* gmax, int32_t* dst, int32_t* cnt) {
+  const int32_t top = (int32_t)(0xffffffffu - (uint32_t)(*gmax & 0xffffffffu));
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < m;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    int32_t i = src ? src[u] : (int32_t)u;
+    bool keep = lam[i] < 0 && i != top;
+    unsigned bm = __ballot_sync(FULL, keep);
+    int base = 0;
+    if ((threadIdx.x & 31) == 0 && bm) base = atomicAdd(cnt, __popc(bm));
+    base = __shfl_sync(FULL, base, 0);
+    if (keep) dst[base + __popc(bm & lanemask_lt())] = i;
+  }
+}
+
+// Exact tail: lambda_i <- DPBruteForce(x_i, P) for the listed points. Block b
+// scans points [b*chunk, (b+1)*chunk); each warp takes listed queries in turn
+// and keeps the smallest (dis, id) key among points ranked above the query;
+// one atomicMin per (warp, query) combines the chunks.
+template <int DT, int METRIC, int W, int CPL>
+__global__ void __launch_bounds__(256) k_dep_bf(const uint8_t* X, int64_t row_bytes, int64_t n, int C,
+                                                 const int32_t* list, int64_t m, const float* rk,
+                                                 int64_t chunk, unsigned long long* best) {
+  constexpr int GR = 32 / W;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int g = lane / W, gl = lane % W;
+  const int64_t j0 = (int64_t)blockIdx.x * chunk;
+  const int64_t j1 = min(n, j0 + chunk);
+  for (int64_t u = wib; u < m; u += nw) {
+    const int32_t q = list[u];
+    uint4 qv[CPL];
+    load_row<W, CPL, false>(X + (int64_t)q * row_bytes, gl, C, qv);
+    unsigned long long mine = KEY_NONE;
+    for (int64_t jb = j0; jb < j1; jb += GR) {
+      int64_t j = jb + g;
+      uint4 r[CPL];
+      if (j < j1) {
+        load_row<W, CPL, false>(X + j * row_bytes, gl, C, r);
+      } else {
+#pragma unroll
+        for (int t = 0; t < CPL; t++) r[t] = make_uint4(0, 0, 0, 0);
+      }
+      float dv = group_dis<DT, METRIC, W, CPL>(qv, r);
+      if (gl == 0 && j < j1 && j != q && ranks_above(rk, (int32_t)j, q)) {
+        unsigned long long kk = make_key(dv, (int32_t)j);
+        mine = kk < mine ? kk : mine;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      unsigned long long o = __shfl_xor_sync(FULL, mine, off);
+      mine = o < mine ? o : mine;
+    }
+    if (lane == 0 && mine != KEY_NONE) atomicMin(best + u, mine);
+  }
+}
+
+__global__ void k_fill_u64(unsigned long long* p, int64_t m, unsigned long long v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+__global__ void k_dep_bf_finish(const int32_t* list, int64_t m, const unsigned long long* best,
+                                int metric, int32_t* lam, float* delta) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < m;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long kk = best[u];
+    if (kk == KEY_NONE) continue;
+    int32_t q = list[u];
+    lam[q] = key_id(kk);
+    delta[q] = out_dist(key_dis(kk), metric);
+  }
+}
+
+template <int DT, int METRIC, int W, int CPL>
+static cudaError_t launch_dep_bf_inst(const DataView& dv, const int32_t* list, int64_t m,
+                                      const float* rk, unsigned long long* best, cudaStream_t st) {
+  // chunk: enough blocks to fill the GPU, rows of a chunk stay in L1/L2
+  int64_t blocks_target = (int64_t)num_sms() * 4;
+  int64_t chunk = (dv.n + blocks_target - 1) / blocks_target;
+  if (chunk < 256) chunk = 256;
+  int64_t grid = (dv.n + chunk - 1) / chunk;
+  k_dep_bf<DT, METRIC, W, CPL><<<(unsigned)grid, 256, 0, st>>>(dv.X, dv.row_bytes, dv.n, dv.C, list, m, rk,
+                                                               chunk, best);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int64_t m,
+                                  const float* rank_key, unsigned long long* best, int32_t* lam,
+                                  float* delta, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  Layout L;
+  if (!pick_layout(dv.dtype, dv.metric, dv.d, &L)) return cudaErrorNotSupported;
+  k_fill_u64<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(best, m, KEY_NONE);
+  cudaError_t e = cudaErrorNotSupported;
+#define PECANN_DINST(DT, MET)                                                            \
+  if (L.W == 8)                                                                          \
+    e = launch_dep_bf_inst<DT, MET, 8, 1>(dv, d_list, m, rank_key, best, st);            \
+  else if (L.W == 16)                                                                    \
+    e = launch_dep_bf_inst<DT, MET, 16, 1>(dv, d_list, m, rank_key, best, st);           \
+  else if (L.CPL == 1)                                                                   \
+    e = launch_dep_bf_inst<DT, MET, 32, 1>(dv, d_list, m, rank_key, best, st);           \
+  else if (L.CPL == 2)                                                                   \
+    e = launch_dep_bf_inst<DT, MET, 32, 2>(dv, d_list, m, rank_key, best, st);           \
+  else if (L.CPL == 3)                                                                   \
+    e = launch_dep_bf_inst<DT, MET, 32, 3>(dv, d_list, m, rank_key, best, st);           \
+  else if (L.CPL == 4)                                                                   \
+    e = launch_dep_bf_inst<DT, MET, 32, 4>(dv, d_list, m, rank_key, best, st);           \
+  else                                                                                   \
+    e = launch_dep_bf_inst<DT, MET, 32, 8>(dv, d_list, m, rank_key, best, st);
+  if (dv.dtype == DT_F32 && dv.metric == MET_L2) {
+    PECANN_DINST(DT_F32, MET_L2)
+  } else if (dv.dtype == DT_F32 && dv.metric == MET_IP) {
+    PECANN_DINST(DT_F32, MET_IP)
+  } else if (dv.dtype == DT_U8) {
+    if (L.W == 8)
+      e = launch_dep_bf_inst<DT_U8, MET_L2, 8, 1>(dv, d_list, m, rank_key, best, st);
+    else
+      e = launch_dep_bf_inst<DT_U8, MET_L2, 16, 1>(dv, d_list, m, rank_key, best, st);
+  }
+#undef PECANN_DINST
+  if (e != cudaSuccess) return e;
+  k_dep_bf_finish<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(d_list, m, best, dv.metric, lam, delta);
+  return cudaGetLastError();
+}
+
+// rho'_i = rho_i k / sum_{j in N_i} rho_j (Sec. 4.2), from a copy of the raw
+// densities; the normalised value is also the rank key.
+__global__ void k_normalize_density(int64_t n, int k, const int32_t* knn_ids, const float* raw, float* rho,
+                                    float* rk) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int t = 0; t < k; t++) s = __fadd_rn(s, raw[knn_ids[i * k + t]]);
+    float r = __fdiv_rn(__fmul_rn(raw[i], (float)k), s);
+    rho[i] = r;
+    rk[i] = r;
+  }
+}
+
+}  // namespace pecann

@@ -1,0 +1,92 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pecann.h"
+
+namespace pecann {
+
+// Search modes of the beam-search kernel (epilogue selection).
+enum : int { MODE_RAW = 0, MODE_KNN = 1, MODE_DEP = 2, MODE_BUILD = 3 };
+
+struct SearchArgs {
+  const uint8_t* X;   // rows
+  int64_t row_bytes;  // bytes per row
+  int64_t n;
+  int C;              // 16-byte chunks per row
+  const int32_t* G;   // n x R
+  int R;
+  const int32_t* queries;  // nq query ids, or NULL for 0..nq-1
+  int64_t nq;
+  const int32_t* S;   // start set, or NULL for {query}
+  int nS;
+  int Lw;             // beam width
+  int log2h;          // seen-filter slots = 1 << log2h
+  int stage;          // candidate staging entries per warp (>= max(R, nS))
+  int vcap;           // BUILD: visited points kept
+  int mode;
+  int metric;
+  int warp_bytes;     // shared memory per warp
+  // RAW / KNN outputs
+  int k;
+  int32_t* out_ids;
+  float* out_dis;
+  int32_t* out_cnt;
+  float* rho;
+  float* rkey;
+  int density_fn;
+  int32_t* fb_list;   // KNN: queries whose search returned < k points
+  int32_t* fb_cnt;
+  // DEP
+  const float* rank_key;
+  int32_t* lam;
+  float* delta;
+  // BUILD
+  int32_t* vis_ids;
+  float* vis_dis;
+  int32_t* vis_cnt;
+  int* err;
+};
+
+struct DataView {
+  const uint8_t* X;
+  int64_t n;
+  int d;
+  int dtype;
+  int metric;
+  int64_t row_bytes;
+  int C;  // 16-byte chunks
+};
+
+// Distance-kernel layout for a dataset: W lanes per row, CPL chunks per lane.
+struct Layout {
+  int W;
+  int CPL;
+};
+bool pick_layout(int dtype, int metric, int d, Layout* out);
+
+// Shared memory needed per warp by the search kernel.
+int search_warp_bytes(int Lw, int log2h, int stage, int vcap, bool build);
+
+// Launch the beam-search kernel. Returns a CUDA error (cudaSuccess on success).
+cudaError_t launch_search(const DataView& dv, SearchArgs a, cudaStream_t st);
+
+// Exact k-NN by brute force for the queries listed in d_list[0..*d_cnt).
+cudaError_t launch_bruteforce_knn(const DataView& dv, const int32_t* d_list, const int32_t* d_cnt,
+                                  int64_t max_list, int k, int32_t* knn_ids, float* knn_dist,
+                                  float* rho, float* rkey, int density_fn, int* err, cudaStream_t st);
+
+// DPBruteForce over all points for the queries in d_list[0..m).
+cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int64_t m,
+                                  const float* rank_key, unsigned long long* best, int32_t* lam,
+                                  float* delta, cudaStream_t st);
+
+int num_sms();
+void set_last_error(const std::string& s);
+
+}  // namespace pecann

@@ -1,0 +1,76 @@
+"""The C ABI library loads and exports every symbol declared in
+include/pecann.h; host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2312_03940_gb300 import build as pbuild
+from paper_2312_03940_gb300 import pecann as pc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    try:
+        path = pbuild.build()
+    except (RuntimeError, FileNotFoundError) as e:  # no nvcc on this machine
+        pytest.skip(f"cannot build the CUDA library here: {e}")
+    return pc.load_library(path)
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "pecann.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"PECANN_API[^;]*?\b(pecann_\w+)\s*\(", text, re.S)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(names) == sorted(pc.EXPORTS)
+
+
+def test_params_default_and_strings(lib):
+    p = pc.params()
+    assert (p.k, p.R, p.L_search, p.dep_threshold, p.max_dep_beam) == (16, 32, 64, 300, 8192)
+    assert abs(p.alpha - 1.1) < 1e-6 and abs(p.batch_frac - 0.02) < 1e-7
+    assert lib.pecann_status_string(pc.EINVAL) == b"invalid argument"
+    assert lib.pecann_version() >= 100
+
+
+def test_struct_layout_matches_header(lib):
+    # pecann_params: 20 four-byte fields, then a uint64 -> 88 bytes
+    assert ctypes.sizeof(pc.PecannParams) == 88
+    assert ctypes.sizeof(pc.PecannDataset) == 48
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    p = pc.params()
+    ds = pc.PecannDataset(None, 100, 32, pc.F32, pc.L2, 0, None, None)
+    st = lib.pecann_density(ctypes.byref(ds), None, ctypes.byref(p), None, None, None, None, None, 0, None)
+    assert st == pc.EINVAL
+    assert b"NULL" in lib.pecann_last_error()
+    # misaligned rows, bad d, bad dtype: all caught before any GPU work
+    ds = pc.PecannDataset(8, 100, 32, pc.F32, pc.L2, 0, None, None)
+    assert lib.pecann_density(ctypes.byref(ds), None, ctypes.byref(p), None, None, None, None, None, 0,
+                              None) == pc.EINVAL
+    ds = pc.PecannDataset(256, 100, 30, pc.F32, pc.L2, 0, None, None)
+    assert lib.pecann_search(ctypes.byref(ds), None, 8, None, 0, None, 0, 8, 4, None, None, None, None, None, 0,
+                             None) == pc.EINVAL
+    ds = pc.PecannDataset(256, 100, 512, pc.U8, pc.L2, 0, None, None)
+    g = ctypes.c_void_p(256)
+    st = lib.pecann_search(ctypes.byref(ds), g, 8, g, 1, None, 0, 8, 4, g, g, g, None, g, 1 << 20, None)
+    assert st == pc.EUNSUPPORTED
+
+
+def test_workspace_size_is_host_only(lib):
+    p = pc.params(R=64, L_build=128)
+    ds = pc.PecannDataset(256, 1_000_000, 128, pc.U8, pc.L2, 0, None, None)
+    b = ctypes.c_size_t(0)
+    assert lib.pecann_workspace_size(ctypes.byref(ds), ctypes.byref(p), ctypes.byref(b)) == pc.OK
+    assert 16 * 1_000_000 < b.value < 1 << 31
