@@ -137,6 +137,10 @@ PECANN_API const char* pecann_last_error(void);
 /* Library version, as major*10000 + minor*100 + patch. */
 PECANN_API int32_t pecann_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+   threads, all devices). Lets a caller count the kernels of a call. */
+PECANN_API int64_t pecann_kernel_launches(void);
+
 /* Workspace bytes that are enough for every call below on this dataset and
    these parameters (host call; no GPU work). */
 PECANN_API pecann_status pecann_workspace_size(const pecann_dataset* ds, const pecann_params* p, size_t* bytes);

@@ -75,6 +75,8 @@ def _load():
         _lib.orc_robust_prune.restype = i32
         _lib.orc_build_graph.argtypes = [P, i32, i32, f32, vp, i32, f32, i32, vp, ctypes.c_int]
         _lib.orc_build_graph.restype = ctypes.c_int
+        _lib.orc_search_counts.argtypes = [P, vp, i32, i32, vp, i64, vp, vp, ctypes.c_int]
+        _lib.orc_search_counts.restype = ctypes.c_int
         _lib.orc_batch_cap.argtypes = [i64, f32]
         _lib.orc_batch_cap.restype = i64
     return _lib
@@ -199,6 +201,18 @@ def robust_prune(P: Points, p: int, cand, alpha: float, R: int) -> np.ndarray:
     out = np.full(R, -1, np.int32)
     m = _load().orc_robust_prune(P.ptr, p, _p(cand), cand.size, np.float32(alpha), R, _p(out))
     return out[:m].copy()
+
+
+def search_counts(P: Points, G: np.ndarray, queries, L: int, threads: int | None = None):
+    """Per query: (expansions incl. the query's own out-list, distinct
+    distance evaluations) of Algorithm 1 with start set {q}, beam L."""
+    G = np.ascontiguousarray(G, dtype=np.int32)
+    q = np.ascontiguousarray(np.asarray(queries, dtype=np.int32).reshape(-1))
+    e = np.zeros(q.size, np.int64)
+    c = np.zeros(q.size, np.int64)
+    _load().orc_search_counts(P.ptr, _p(G), G.shape[1], L, _p(q), q.size, _p(e), _p(c),
+                              threads or default_threads())
+    return e, c
 
 
 def batch_cap(n: int, batch_frac: float) -> int:

@@ -57,6 +57,37 @@ def exact_knn(X: np.ndarray, k: int, metric: int = L2, block: int = 512):
     return ids, dist
 
 
+def exact_knn_queries(X: np.ndarray, rows: np.ndarray, k: int, metric: int = L2, chunk: int = 65536):
+    """Exact k nearest neighbours (FP64, self excluded, ties by smaller id) of
+    the sampled points `rows` over all of X, scanning X in chunks.
+    Returns ids (m,k) int64 and dist (m,k) float64."""
+    rows = np.asarray(rows, dtype=np.int64)
+    Q = X[rows].astype(np.float64)
+    qn = (Q * Q).sum(1)
+    best_d = np.full((len(rows), k), np.inf)
+    best_i = np.full((len(rows), k), -1, np.int64)
+    for c0 in range(0, X.shape[0], chunk):
+        Y = X[c0:c0 + chunk].astype(np.float64)
+        if metric == IP:
+            D = 1.0 - Q @ Y.T
+        else:
+            D = qn[:, None] + (Y * Y).sum(1)[None, :] - 2.0 * (Q @ Y.T)
+            np.maximum(D, 0.0, out=D)
+        ids = np.arange(c0, c0 + Y.shape[0])
+        D[rows[:, None] == ids[None, :]] = np.inf
+        cand_d = np.concatenate([best_d, D], 1)
+        cand_i = np.concatenate([best_i, np.broadcast_to(ids, D.shape)], 1)
+        # sort each row by (distance, id): a stable sort keeps the earlier
+        # (smaller) ids first among equal distances
+        idx = np.argsort(cand_d, axis=1, kind="stable")
+        cand_d = np.take_along_axis(cand_d, idx, 1)
+        cand_i = np.take_along_axis(cand_i, idx, 1)
+        best_d, best_i = cand_d[:, :k], cand_i[:, :k]
+    if metric == L2:
+        best_d = np.sqrt(best_d)
+    return best_i, best_d
+
+
 def density(dist: np.ndarray, fn: str = "kth", normalize: bool = False, ids: np.ndarray | None = None):
     """Density from the sorted k-NN distances (Sec. 4.2, Appendix A).
     Returns (rho, key): key ranks the points (equal to rho except for exp-sum,

@@ -175,6 +175,9 @@ typedef struct {
   int64_t n;
   int32_t* in_beam; /* == stamp iff the point is in L */
   int32_t* in_vis;  /* == stamp iff the point is in V */
+  int32_t* in_seen; /* == stamp iff D(x_q, point) was computed in this search */
+  int64_t n_exp;    /* expansions of the last search (|V| without the query) */
+  int64_t n_eval;   /* distinct points whose distance the last search computed */
   int32_t stamp;
   item* beam;
   int64_t beam_cap;
@@ -189,11 +192,13 @@ static void ws_init(search_ws* ws, int64_t n) {
   ws->n = n;
   ws->in_beam = (int32_t*)calloc((size_t)n, sizeof(int32_t));
   ws->in_vis = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  ws->in_seen = (int32_t*)calloc((size_t)n, sizeof(int32_t));
 }
 
 static void ws_free(search_ws* ws) {
   free(ws->in_beam);
   free(ws->in_vis);
+  free(ws->in_seen);
   free(ws->beam);
   free(ws->vis);
   free(ws->tmp);
@@ -228,6 +233,10 @@ static void add_out_neighbors(search_state* st, int64_t p) {
     ws->beam[st->nb].id = y;
     st->nb++;
     ws->in_beam[y] = ws->stamp;
+    if (ws->in_seen[y] != ws->stamp) {
+      ws->in_seen[y] = ws->stamp;
+      ws->n_eval++;
+    }
   }
 }
 
@@ -252,6 +261,8 @@ static int64_t greedy_search(const orc_points* P, const int32_t* G, int32_t R, i
                              search_ws* ws, item* out, item** vis_out, int64_t* nvis_out) {
   search_state st = {P, G, R, q, ws, 0};
   ws->stamp++;
+  ws->n_exp = 0;
+  ws->n_eval = 0;
   int64_t nv = 0;
   /* V <- {q}: the query is visited first and never enters the beam. */
   ws->in_vis[q] = ws->stamp;
@@ -269,6 +280,8 @@ static int64_t greedy_search(const orc_points* P, const int32_t* G, int32_t R, i
     ws->beam[st.nb].id = y;
     st.nb++;
     ws->in_beam[y] = ws->stamp;
+    ws->in_seen[y] = ws->stamp;
+    ws->n_eval++;
   }
   if (q_in_S) {
     /* the query is the first point popped: its out-neighbours join L */
@@ -288,6 +301,7 @@ static int64_t greedy_search(const orc_points* P, const int32_t* G, int32_t R, i
     ws->in_vis[pstar.id] = ws->stamp;       /* V <- V u {p*} */
     grow(&ws->vis, &ws->vis_cap, nv + 1);
     ws->vis[nv++] = pstar;
+    ws->n_exp++;
     keep_closest(&st, Lw);                  /* |L| > Lw: keep the Lw closest */
   }
   /* the k closest points of (L u V) \ {q} */
@@ -308,6 +322,42 @@ static int64_t greedy_search(const orc_points* P, const int32_t* G, int32_t R, i
   /* leave the stamp arrays clean for the next search of this thread */
   for (int64_t b = 0; b < st.nb; b++) ws->in_beam[ws->beam[b].id] = 0;
   return cnt;
+}
+
+typedef struct {
+  const orc_points* P;
+  const int32_t* G;
+  int32_t R, L;
+  const int32_t* queries;
+  int64_t* n_exp;
+  int64_t* n_eval;
+  search_ws* ws;
+} count_ctx;
+
+static void count_body(void* c, int64_t u, int tid) {
+  count_ctx* x = (count_ctx*)c;
+  int32_t q = x->queries[u];
+  int32_t S[1] = {q};
+  greedy_search(x->P, x->G, x->R, q, S, 1, x->L, 0, &x->ws[tid], NULL, NULL, NULL);
+  x->n_exp[u] = x->ws[tid].n_exp;
+  x->n_eval[u] = x->ws[tid].n_eval;
+}
+
+/* Work of Algorithm 1 per query (start set {x_q}, beam L): expansions
+   (out-lists read, the query's own included) and distinct points whose
+   distance was computed. These define the algorithmic bytes of a search. */
+int orc_search_counts(const orc_points* P, const int32_t* G, int32_t R, int32_t L,
+                      const int32_t* queries, int64_t m, int64_t* n_exp, int64_t* n_eval,
+                      int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  search_ws* ws = (search_ws*)malloc(sizeof(search_ws) * nthreads);
+  for (int t = 0; t < nthreads; t++) ws_init(&ws[t], P->n);
+  count_ctx c = {P, G, R, L, queries, n_exp, n_eval, ws};
+  parallel_for(m, nthreads, count_body, &c);
+  for (int u = 0; u < m; u++) n_exp[u] += 1; /* the query's own out-list */
+  for (int t = 0; t < nthreads; t++) ws_free(&ws[t]);
+  free(ws);
+  return 0;
 }
 
 /* Exact k nearest points of x_q over P \ {q} by brute force (used where a
@@ -903,7 +953,7 @@ int orc_build_graph(const orc_points* P, int32_t R, int32_t L, float alpha, cons
       V[t] = NULL;
     }
     pos += m;
-    bsz *= 2;
+    if (bsz < cap) bsz *= 2; /* the doubling stops at the cap */
   }
   free(tgt_begin);
   free(pairs);

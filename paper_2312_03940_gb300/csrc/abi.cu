@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -30,6 +31,13 @@ __global__ void k_normalize_density(int64_t n, int k, const int32_t* knn_ids, co
                                     float* rk);
 
 static thread_local std::string g_last_error;
+static thread_local const char* g_where = "";
+
+void set_where(const char* w) { g_where = w; }
+const char* get_where() { return g_where; }
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(const std::string& s) { g_last_error = s; }
 
@@ -98,7 +106,8 @@ static pecann_status cuda_status(cudaError_t e, const char* what) {
     set_last_error(std::string(what) + ": unsupported combination");
     return PECANN_EUNSUPPORTED;
   }
-  set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+  set_last_error(std::string(what) + ": " + cudaGetErrorString(e) + (*g_where ? std::string(" (at ") + g_where + ")" : ""));
+  g_where = "";
   return PECANN_ECUDA;
 }
 
@@ -176,6 +185,8 @@ const char* pecann_status_string(int s) {
 const char* pecann_last_error(void) { return g_last_error.c_str(); }
 
 int32_t pecann_version(void) { return 100; }
+
+int64_t pecann_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 pecann_status pecann_workspace_size(const pecann_dataset* ds, const pecann_params* p, size_t* bytes) {
   if (!ds || !p || !bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
@@ -317,7 +328,7 @@ pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, c
     if ((e = cudaMemcpyAsync(raw, d_density, (size_t)dv.n * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
       return cuda_status(e, "copy");
     unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
-    k_normalize_density<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, raw, d_density, d_rank_key);
+    k_normalize_density<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, raw, d_density, d_rank_key); note_launch();
     if ((s = cuda_status(cudaGetLastError(), "normalize"))) return s;
   }
   return PECANN_OK;
@@ -350,11 +361,11 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
   if (e != cudaSuccess) return cuda_status(e, "memset");
   const unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
   // the maximum-rank point has no dependent point
-  k_rank_max<<<blocks, 256, 0, st>>>(dv.n, d_rank_key, &h->gmax);
+  k_rank_max<<<blocks, 256, 0, st>>>(dv.n, d_rank_key, &h->gmax); note_launch();
   // round 0: lambda_i <- DPBruteForce(x_i, N_i)
-  k_dep_round0<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, d_knn_dist, d_rank_key, d_dep, d_dep_dist);
+  k_dep_round0<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, d_knn_dist, d_rank_key, d_dep, d_dep_dist); note_launch();
   // P_unfinished, the maximum skipped
-  k_compact_unfinished<<<blocks, 256, 0, st>>>(nullptr, dv.n, d_dep, &h->gmax, U0, &h->counts[1]);
+  k_compact_unfinished<<<blocks, 256, 0, st>>>(nullptr, dv.n, d_dep, &h->gmax, U0, &h->counts[1]); note_launch();
   if ((s = cuda_status(cudaGetLastError(), "round 0"))) return s;
   int32_t nu = 0;
   if ((e = cudaMemcpyAsync(&nu, &h->counts[1], 4, cudaMemcpyDeviceToHost, st)) == cudaSuccess)
@@ -388,7 +399,7 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
     if ((s = cuda_status(launch_search(dv, a, st), "dependent search"))) return s;
     if ((e = cudaMemsetAsync(&h->counts[2], 0, 4, st)) != cudaSuccess) return cuda_status(e, "memset");
     unsigned ub = (unsigned)std::min<int64_t>((nu + 255) / 256, (int64_t)num_sms() * 8);
-    k_compact_unfinished<<<ub, 256, 0, st>>>(U0, nu, d_dep, &h->gmax, U1, &h->counts[2]);
+    k_compact_unfinished<<<ub, 256, 0, st>>>(U0, nu, d_dep, &h->gmax, U1, &h->counts[2]); note_launch();
     if ((s = cuda_status(cudaGetLastError(), "compact"))) return s;
     if ((e = cudaMemcpyAsync(&nu, &h->counts[2], 4, cudaMemcpyDeviceToHost, st)) == cudaSuccess)
       e = cudaStreamSynchronize(st);

@@ -447,6 +447,7 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     d_order = order;
   }
+  set_where("build: clear graph and counters");
   if ((e = cudaMemsetAsync(G, 0xff, (size_t)n * R * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(cnt, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(fillc, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
@@ -515,6 +516,7 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
     int64_t m = std::min(std::min(bsz, cap), n - pos);
     a.queries = d_order + pos;
     a.nq = m;
+    set_where("build: batch search");
     if ((e = launch_search(dv, a, st)) != cudaSuccess) return e;
     b.batch = d_order + pos;
     b.m = m;
@@ -523,34 +525,45 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
       constexpr int W = decltype(wv)::value, CPL = decltype(cpl)::value;
       auto kn = k_prune_new<DT, MET, W, CPL>;
       size_t sm = new_smem_warp * new_wpb;
+      set_where("build: prune attribute");
       cudaError_t ee = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (ee != cudaSuccess) return ee;
+      set_where("build: prune launch");
       int64_t blocks = std::min<int64_t>((m + new_wpb - 1) / new_wpb, (int64_t)sms * 8);
-      kn<<<(unsigned)blocks, new_wpb * 32, sm, st>>>(b);
+      kn<<<(unsigned)blocks, new_wpb * 32, sm, st>>>(b); note_launch();
       if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+      set_where("build: reverse-edge counters");
       if ((ee = cudaMemsetAsync(counters, 0, 64, st)) != cudaSuccess) return ee;
       int64_t edges = m * R;
       unsigned eb = (unsigned)std::min<int64_t>((edges + 255) / 256, (int64_t)sms * 16);
-      k_rev_count<<<eb, 256, 0, st>>>(b);
-      k_rev_offsets<<<eb, 256, 0, st>>>(b);
-      k_rev_fill<<<eb, 256, 0, st>>>(b);
+      set_where("build: reverse-edge count");
+      k_rev_count<<<eb, 256, 0, st>>>(b); note_launch();
+      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+      set_where("build: reverse-edge offsets");
+      k_rev_offsets<<<eb, 256, 0, st>>>(b); note_launch();
+      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+      set_where("build: reverse-edge fill");
+      k_rev_fill<<<eb, 256, 0, st>>>(b); note_launch();
+      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
       auto ka = k_rev_apply<DT, MET, W, CPL>;
       size_t sm2 = rev_smem_warp * rev_wpb;
+      set_where("build: reverse-edge apply");
       if ((ee = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
         return ee;
       unsigned ab = (unsigned)std::min<int64_t>((edges + rev_wpb - 1) / rev_wpb, (int64_t)sms * 8);
-      ka<<<ab, rev_wpb * 32, sm2, st>>>(b);
-      k_rev_apply_big<DT, MET, W, CPL><<<BIG_WARPS, 32, 0, st>>>(b);
+      ka<<<ab, rev_wpb * 32, sm2, st>>>(b); note_launch();
+      k_rev_apply_big<DT, MET, W, CPL><<<BIG_WARPS, 32, 0, st>>>(b); note_launch();
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
     pos += m;
-    bsz *= 2;
+    bsz = std::min(2 * bsz, cap);  // doubling stops at the cap (no overflow)
   }
   if (d_degree) {
-    k_degree<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8), 256, 0, st>>>(n, R, G, d_degree);
+    k_degree<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8), 256, 0, st>>>(n, R, G, d_degree); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  set_where("build: final synchronize");
   return cudaStreamSynchronize(st);
 }
 

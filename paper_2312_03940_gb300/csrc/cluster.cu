@@ -161,21 +161,23 @@ cudaError_t run_cluster(int64_t n, const float* rho, const int32_t* lam, const f
   if (center_fn == PECANN_CENTER_PRODUCT) {
     if ((e = cudaMemsetAsync(nonnoise, 0, 8, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(hist, 0, 65536 * 4, st)) != cudaSuccess) return e;
-    k_center_keys<<<blocks, threads, 0, st>>>(n, rho, delta, rho_min, keys, nonnoise);
-    k_select_init<<<1, 1, 0, st>>>(s, nonnoise, n_clusters);
+    k_center_keys<<<blocks, threads, 0, st>>>(n, rho, delta, rho_min, keys, nonnoise); note_launch();
+    k_select_init<<<1, 1, 0, st>>>(s, nonnoise, n_clusters); note_launch();
     for (int pass = 0; pass < 4; pass++) {
-      k_select_hist<<<blocks, threads, 0, st>>>(n, keys, s, pass, hist);
-      k_select_pick<<<1, 1024, 0, st>>>(s, pass, hist);
+      k_select_hist<<<blocks, threads, 0, st>>>(n, keys, s, pass, hist); note_launch();
+      k_select_pick<<<1, 1024, 0, st>>>(s, pass, hist); note_launch();
     }
   }
   k_cluster_parent<<<blocks, threads, 0, st>>>(n, rho, delta, lam, center_fn, rho_min, delta_min, keys, s,
-                                               labels);
+                                               labels); note_launch();
   int sweeps = 1;
   while (((int64_t)1 << sweeps) < n) sweeps++;
-  for (int it = 0; it <= sweeps; it++) k_jump<<<blocks, threads, 0, st>>>(n, labels);
+  for (int it = 0; it <= sweeps; it++) {
+    k_jump<<<blocks, threads, 0, st>>>(n, labels); note_launch();
+  }
   if (d_roots) {
     if ((e = cudaMemsetAsync(d_roots, 0, 8, st)) != cudaSuccess) return e;
-    k_count_roots<<<blocks, threads, 0, st>>>(n, labels, d_roots);
+    k_count_roots<<<blocks, threads, 0, st>>>(n, labels, d_roots); note_launch();
   }
   return cudaGetLastError();
 }

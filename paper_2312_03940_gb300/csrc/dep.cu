@@ -135,7 +135,7 @@ static cudaError_t launch_dep_bf_inst(const DataView& dv, const int32_t* list, i
   if (chunk < 256) chunk = 256;
   int64_t grid = (dv.n + chunk - 1) / chunk;
   k_dep_bf<DT, METRIC, W, CPL><<<(unsigned)grid, 256, 0, st>>>(dv.X, dv.row_bytes, dv.n, dv.C, list, m, rk,
-                                                               chunk, best);
+                                                               chunk, best); note_launch();
   return cudaGetLastError();
 }
 
@@ -145,7 +145,7 @@ cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int
   if (m <= 0) return cudaSuccess;
   Layout L;
   if (!pick_layout(dv.dtype, dv.metric, dv.d, &L)) return cudaErrorNotSupported;
-  k_fill_u64<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(best, m, KEY_NONE);
+  k_fill_u64<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(best, m, KEY_NONE); note_launch();
   cudaError_t e = cudaErrorNotSupported;
 #define PECANN_DINST(DT, MET)                                                            \
   if (L.W == 8)                                                                          \
@@ -174,7 +174,7 @@ cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int
   }
 #undef PECANN_DINST
   if (e != cudaSuccess) return e;
-  k_dep_bf_finish<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(d_list, m, best, dv.metric, lam, delta);
+  k_dep_bf_finish<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(d_list, m, best, dv.metric, lam, delta); note_launch();
   return cudaGetLastError();
 }
 

@@ -87,6 +87,11 @@ cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int
                                   float* delta, cudaStream_t st);
 
 int num_sms();
+// Counts the kernels the library launches (reported by pecann_kernel_launches).
+void note_launch();
 void set_last_error(const std::string& s);
+// Name of the step that issued the CUDA call that failed last (for messages).
+void set_where(const char* w);
+const char* get_where();
 
 }  // namespace pecann

@@ -444,16 +444,22 @@ static cudaError_t launch_inst(const SearchArgs& a, cudaStream_t st) {
   size_t smem = (size_t)wpb * a.warp_bytes;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    set_where("search: shared-memory attribute");
+    return e;
+  }
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    set_where("search: occupancy query");
+    return e;
+  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t want = (a.nq + wpb - 1) / wpb;
   int64_t cap = (int64_t)num_sms() * per_sm;
   int grid = (int)(want < cap ? want : cap);
   if (grid < 1) grid = 1;
-  kern<<<grid, wpb * 32, smem, st>>>(a);
+  kern<<<grid, wpb * 32, smem, st>>>(a); note_launch();
   return cudaGetLastError();
 }
 
@@ -554,7 +560,7 @@ static cudaError_t launch_bf_inst(const BfKnnArgs& b, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = num_sms() * 2;
-  kern<<<grid, wpb * 32, smem, st>>>(b);
+  kern<<<grid, wpb * 32, smem, st>>>(b); note_launch();
   return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ class PecannDataset(ctypes.Structure):
 
 
 EXPORTS = ["pecann_params_default", "pecann_status_string", "pecann_last_error", "pecann_version",
+           "pecann_kernel_launches",
            "pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
            "pecann_dependent_points", "pecann_cluster"]
 
@@ -75,6 +76,8 @@ def load_library(path: str | None = None):
     lib.pecann_last_error.restype = ctypes.c_char_p
     lib.pecann_version.argtypes = []
     lib.pecann_version.restype = i32
+    lib.pecann_kernel_launches.argtypes = []
+    lib.pecann_kernel_launches.restype = i64
     lib.pecann_workspace_size.argtypes = [D, P, ctypes.POINTER(sz)]
     lib.pecann_search.argtypes = [D, vp, i32, vp, i64, vp, i32, i32, i32, vp, vp, vp, P, vp, sz, vp]
     lib.pecann_build_graph.argtypes = [D, P, vp, vp, vp, vp, sz, vp]
@@ -150,6 +153,11 @@ class Dataset:
     @property
     def ref(self):
         return ctypes.byref(self.c)
+
+
+def pecann_kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().pecann_kernel_launches())
 
 
 def pecann_workspace_size(ds: Dataset, p: PecannParams) -> int:
