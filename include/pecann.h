@@ -92,7 +92,7 @@ typedef struct {
   int32_t L_search;          /* beam width of the k-NN searches            density            */
   int32_t L_dep;             /* initial k_dep of the doubling rounds (L_d) dependent          */
   float alpha;               /* RobustPrune slack, >= 1                    build              */
-  int32_t n_start;           /* sampled start points, 1..min(n, L_build)  build              */
+  int32_t n_start;           /* sampled start points, 1..min(n, 65536)     build              */
   float batch_frac;          /* batch size cap as a fraction of n (0.02)   build              */
   int32_t visit_cap;         /* closest visited points kept per build search (0: 2*L_build)   */
   int32_t dep_threshold;     /* doubling continues while > this many are unfinished (300)     */
@@ -105,7 +105,12 @@ typedef struct {
   float delta_min;           /* threshold center                          cluster            */
   int32_t n_clusters;        /* product center                            cluster            */
   int32_t hash_slots;        /* per-query seen-filter slots (power of 2; 0 = automatic)      */
-  int32_t reserved0;
+  int32_t collect_work;      /* != 0: pecann_search / pecann_density leave the sums of
+                                expansions and of distance evaluations as two int64 at
+                                byte offset 80 of the workspace                          */
+  int32_t build_passes;      /* 1, or 2: a first insertion pass pruning with alpha = 1,
+                                then a second over all points with alpha   build              */
+  int32_t reserved1;
   uint64_t seed;             /* insertion order when none is given         build              */
 } pecann_params;
 
@@ -125,7 +130,8 @@ typedef struct {
 /* Fills the defaults: k 16, R 32, L_build 64, L_search 64, L_dep 64,
    alpha 1.1, n_start 16, batch_frac 0.02, visit_cap 0, dep_threshold 300,
    max_dep_rounds 30, max_dep_beam 8192, kth density, no normalisation,
-   product center, rho_min 0, delta_min 0, n_clusters 1, seed 0. */
+   product center, rho_min 0, delta_min 0, n_clusters 1, hash_slots 0,
+   collect_work 0, build_passes 1, seed 0. */
 PECANN_API void pecann_params_default(pecann_params* p);
 
 /* Static string for a status code. */
@@ -148,8 +154,10 @@ PECANN_API pecann_status pecann_workspace_size(const pecann_dataset* ds, const p
 /*
  * Greedy beam search, Algorithm 1, for m query points of the dataset.
  * Query q = d_queries[i] starts from the set {q} (its out-neighbours are the
- * first candidates) when d_start is NULL, else from the n_start ids of
- * d_start; the query itself never enters the beam and is never returned.
+ * first candidates) when d_start is NULL, else from the n_start (<= 65536)
+ * ids of d_start, all of which enter the beam before the first prune keeps
+ * the L closest; a query that is one of them is expanded first. The query
+ * itself never occupies a beam slot and is never returned.
  * Beam width L (1 <= L <= 8192), result size k (1 <= k <= L).
  * Output per query i: d_ids[i*k .. i*k+k) and d_dis[...] -- the min(k, |beam|)
  * closest points found, ascending by (dis, id), -1 / +inf padded -- and

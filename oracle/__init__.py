@@ -73,7 +73,7 @@ def _load():
         _lib.orc_cluster.restype = i64
         _lib.orc_robust_prune.argtypes = [P, i64, vp, i64, f32, i32, vp]
         _lib.orc_robust_prune.restype = i32
-        _lib.orc_build_graph.argtypes = [P, i32, i32, f32, vp, i32, f32, i32, vp, ctypes.c_int]
+        _lib.orc_build_graph.argtypes = [P, i32, i32, f32, vp, i32, f32, i32, i32, vp, ctypes.c_int]
         _lib.orc_build_graph.restype = ctypes.c_int
         _lib.orc_search_counts.argtypes = [P, vp, i32, i32, vp, i64, vp, vp, ctypes.c_int]
         _lib.orc_search_counts.restype = ctypes.c_int
@@ -220,12 +220,14 @@ def batch_cap(n: int, batch_frac: float) -> int:
 
 
 def build_graph(P: Points, R: int, L: int, alpha: float, perm: np.ndarray, n_start: int,
-                batch_frac: float = 0.02, visit_cap: int | None = None, threads: int | None = None):
-    """Batched Vamana construction. Returns G (n x R int32, -1 padded)."""
+                batch_frac: float = 0.02, visit_cap: int | None = None, threads: int | None = None,
+                passes: int = 1):
+    """Batched Vamana construction (passes = 2: first pass with alpha = 1).
+    Returns G (n x R int32, -1 padded)."""
     perm = np.ascontiguousarray(perm, dtype=np.int32)
     G = np.empty((P.n, R), np.int32)
     rc = _load().orc_build_graph(P.ptr, R, L, np.float32(alpha), _p(perm), n_start, np.float32(batch_frac),
-                                 visit_cap if visit_cap else 2 * L, _p(G), threads or default_threads())
+                                 visit_cap if visit_cap else 2 * L, passes, _p(G), threads or default_threads())
     if rc:
         raise ValueError("orc_build_graph: bad arguments")
     return G

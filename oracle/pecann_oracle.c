@@ -909,10 +909,10 @@ int64_t orc_batch_cap(int64_t n, float batch_frac) {
  * G (n x R) is written, -1 padded. Returns 0, or 1 on bad arguments.
  */
 int orc_build_graph(const orc_points* P, int32_t R, int32_t L, float alpha, const int32_t* perm,
-                    int32_t n_start, float batch_frac, int32_t visit_cap, int32_t* G,
+                    int32_t n_start, float batch_frac, int32_t visit_cap, int32_t passes, int32_t* G,
                     int nthreads) {
   int64_t n = P->n;
-  if (R < 1 || L < 1 || n_start < 1 || n_start > n || visit_cap < 1) return 1;
+  if (R < 1 || L < 1 || n_start < 1 || n_start > n || visit_cap < 1 || passes < 1 || passes > 2) return 1;
   if (nthreads < 1) nthreads = 1;
   for (int64_t i = 0; i < n * R; i++) G[i] = -1;
   search_ws* ws = (search_ws*)malloc(sizeof(search_ws) * nthreads);
@@ -923,6 +923,9 @@ int orc_build_graph(const orc_points* P, int32_t R, int32_t L, float alpha, cons
   int32_t* pairs = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)(cap * R));
   int64_t* tgt_begin = (int64_t*)malloc(sizeof(int64_t) * (size_t)(cap * R + 1));
   build_ctx c = {P, G, R, L, alpha, perm, n_start, visit_cap, NULL, V, nV, tgt_begin, pairs, ws};
+  for (int32_t pass = 0; pass < passes; pass++) {
+  /* with two passes the first one prunes with alpha = 1 */
+  c.alpha = (passes == 2 && pass == 0) ? 1.0f : alpha;
   int64_t pos = 0, bsz = 1;
   while (pos < n) {
     int64_t m = bsz < cap ? bsz : cap;
@@ -954,6 +957,7 @@ int orc_build_graph(const orc_points* P, int32_t R, int32_t L, float alpha, cons
     }
     pos += m;
     if (bsz < cap) bsz *= 2; /* the doubling stops at the cap */
+  }
   }
   free(tgt_begin);
   free(pairs);

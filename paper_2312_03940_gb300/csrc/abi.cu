@@ -63,6 +63,7 @@ struct WsHeader {
   int32_t counts[14];
   unsigned long long gmax;
   unsigned long long roots;
+  unsigned long long work[2];  // byte offset 80: expansions, distance evaluations
 };
 static const size_t HDR = 256;
 
@@ -166,6 +167,8 @@ void pecann_params_default(pecann_params* p) {
   p->delta_min = 0.0f;
   p->n_clusters = 1;
   p->hash_slots = 0;
+  p->collect_work = 0;
+  p->build_passes = 1;
   p->seed = 0;
 }
 
@@ -213,7 +216,7 @@ pecann_status pecann_search(const pecann_dataset* ds, const int32_t* d_graph, in
   if (!d_graph || !d_ids || !d_dis || !d_count || !ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
   if (R < 1 || R > 256 || L < 1 || L > 8192 || k < 1 || k > L || m < 0)
     return set_last_error("R, L, k or m out of range"), PECANN_EINVAL;
-  if (d_start && (n_start < 1 || n_start > 1024)) return set_last_error("n_start out of range"), PECANN_EINVAL;
+  if (d_start && (n_start < 1 || n_start > 65536)) return set_last_error("n_start out of range"), PECANN_EINVAL;
   if (ws_bytes < HDR) return set_last_error("workspace too small"), PECANN_ENOMEM;
   pecann_params dp;
   pecann_params_default(&dp);
@@ -236,7 +239,7 @@ pecann_status pecann_search(const pecann_dataset* ds, const int32_t* d_graph, in
   a.nS = d_start ? n_start : 0;
   a.Lw = L;
   a.log2h = log2_hash(p, L);
-  a.stage = (std::max(R, a.nS) + 31) & ~31;
+  a.stage = (std::max(R, 64) + 31) & ~31;
   a.mode = MODE_RAW;
   a.metric = dv.metric;
   a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
@@ -245,6 +248,7 @@ pecann_status pecann_search(const pecann_dataset* ds, const int32_t* d_graph, in
   a.out_dis = d_dis;
   a.out_cnt = d_count;
   a.err = &h->err;
+  a.work = p->collect_work ? h->work : nullptr;
   if ((s = cuda_status(launch_search(dv, a, st), "search"))) return s;
   return read_err(&h->err, st);
 }
@@ -258,9 +262,10 @@ pecann_status pecann_build_graph(const pecann_dataset* ds, const pecann_params* 
   if (p->R < 1 || p->R > 256) return set_last_error("R must be in 1..256"), PECANN_EINVAL;
   if (p->L_build < 1 || p->L_build > 1024) return set_last_error("L_build must be in 1..1024"), PECANN_EINVAL;
   if (!(p->alpha >= 1.0f)) return set_last_error("alpha must be >= 1"), PECANN_EINVAL;
-  if (p->n_start < 1 || p->n_start > dv.n || p->n_start > p->L_build || p->n_start > 1024)
-    return set_last_error("n_start must be in 1..min(n, L_build)"), PECANN_EINVAL;
+  if (p->n_start < 1 || p->n_start > dv.n || p->n_start > 65536)
+    return set_last_error("n_start must be in 1..min(n, 65536)"), PECANN_EINVAL;
   if (!(p->batch_frac > 0.0f) || p->batch_frac > 1.0f) return set_last_error("batch_frac must be in (0, 1]"), PECANN_EINVAL;
+  if (p->build_passes != 1 && p->build_passes != 2) return set_last_error("build_passes must be 1 or 2"), PECANN_EINVAL;
   int vcap = p->visit_cap > 0 ? p->visit_cap : 2 * p->L_build;
   if (vcap + p->R > 4096) return set_last_error("visit_cap + R must be <= 4096"), PECANN_EINVAL;
   if (p->hash_slots < 0 || (p->hash_slots & (p->hash_slots - 1)))
@@ -319,6 +324,7 @@ pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, c
   a.fb_list = fb_list;
   a.fb_cnt = &h->counts[0];
   a.err = &h->err;
+  a.work = p->collect_work ? h->work : nullptr;
   if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
   // points whose search returned fewer than k: exact k-NN by brute force
   e = launch_bruteforce_knn(dv, fb_list, &h->counts[0], dv.n, p->k, d_knn_ids, d_knn_dist, d_density,

@@ -494,8 +494,7 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
   a.nS = p.n_start;
   a.Lw = p.L_build;
   a.log2h = log2h;
-  a.stage = std::max(R, p.n_start);
-  a.stage = (a.stage + 31) & ~31;
+  a.stage = (std::max(R, 64) + 31) & ~31;
   a.vcap = vcap;
   a.mode = MODE_BUILD;
   a.metric = dv.metric;
@@ -510,7 +509,11 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
   const size_t rev_smem_warp = (size_t)PRUNE_CAP * 16 + (size_t)R * 4;
   const int rev_wpb = 2;
   const int sms = num_sms();
+  const int passes = p.build_passes == 2 ? 2 : 1;
 
+  for (int pass = 0; pass < passes; pass++) {
+  // two passes: the first prunes with alpha = 1, the second with alpha
+  b.a2 = (passes == 2 && pass == 0) ? 1.0f : p.alpha * p.alpha;
   int64_t pos = 0, bsz = 1;
   while (pos < n) {
     int64_t m = std::min(std::min(bsz, cap), n - pos);
@@ -558,6 +561,7 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
     if (e != cudaSuccess) return e;
     pos += m;
     bsz = std::min(2 * bsz, cap);  // doubling stops at the cap (no overflow)
+  }
   }
   if (d_degree) {
     k_degree<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8), 256, 0, st>>>(n, R, G, d_degree); note_launch();

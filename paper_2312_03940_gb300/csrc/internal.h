@@ -51,6 +51,7 @@ struct SearchArgs {
   float* vis_dis;
   int32_t* vis_cnt;
   int* err;
+  unsigned long long* work;  // optional: [0] expansions, [1] distance evaluations (sums)
 };
 
 struct DataView {

@@ -92,20 +92,21 @@ __device__ __forceinline__ int gather_out(const SearchArgs& a, WarpSmem& w, int3
   return nc;
 }
 
-// Candidate ids from the start set; *q_in_s tells whether the query itself
-// is one of the start points.
-__device__ __forceinline__ int gather_start(const SearchArgs& a, WarpSmem& w, int32_t q, int lane,
+// Candidate ids from the start points S[s0 .. s0 + stage); *q_in_s is set
+// when the query itself is one of them.
+__device__ __forceinline__ int gather_start(const SearchArgs& a, WarpSmem& w, int32_t q, int s0, int lane,
                                             bool* q_in_s) {
   int nc = 0;
   bool has_q = false;
-  for (int b = 0; b < a.nS; b += 32) {
+  const int s1 = min(a.nS, s0 + a.stage);
+  for (int b = s0; b < s1; b += 32) {
     int idx = b + lane;
-    int32_t y = idx < a.nS ? __ldg(a.S + idx) : -1;
+    int32_t y = idx < s1 ? __ldg(a.S + idx) : -1;
     has_q |= __any_sync(FULL, y == q);
     nc = admit(a, w, y, q, nc, lane);
   }
   __syncwarp();
-  *q_in_s = has_q;
+  *q_in_s |= has_q;
   return nc;
 }
 
@@ -312,23 +313,30 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
     // L <- S. A query that is itself in S (always, for the k-NN and
     // dependent searches, whose S is {x_i}) is popped first: its out-list
     // joins L and the query stays out of the beam.
-    bool q_in_s = true;
+    // A start set larger than the staging area goes through the merge in
+    // chunks; keeping the Lw closest of each merge leaves the Lw closest
+    // points of S, which is what the first prune of Algorithm 1 keeps.
+    bool q_in_s = a.S == nullptr;
     int nc = 0;
-    if (a.S) {
-      nc = gather_start(a, w, q, lane, &q_in_s);
+    int64_t evals = 0;
+    for (int s0 = 0; a.S && s0 < a.nS; s0 += a.stage) {
+      nc = gather_start(a, w, q, s0, lane, &q_in_s);
       if (nc) {
         eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
         merge_cands(w, nb, a.Lw, nc, cursor, lane);
-      }
-    }
-    if (q_in_s) {
-      nc = gather_out(a, w, q, q, lane);
-      if (nc) {
-        eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-        merge_cands(w, nb, a.Lw, nc, cursor, lane);
+        evals += nc;
       }
     }
     int64_t iters = 0;
+    if (q_in_s) {
+      nc = gather_out(a, w, q, q, lane);
+      iters = 1;
+      if (nc) {
+        eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
+        merge_cands(w, nb, a.Lw, nc, cursor, lane);
+        evals += nc;
+      }
+    }
     for (;;) {
       // p* <- argmin over L \ V
       int pos = find_unvisited(w.beam, nb, cursor, lane);
@@ -345,11 +353,16 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
       if (nc) {
         eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
         merge_cands(w, nb, a.Lw, nc, cursor, lane);
+        evals += nc;
       }
-      if (++iters > a.n) {
+      if (++iters > a.n + 1) {
         if (lane == 0) set_error(a.err, ERR_NO_PROGRESS);
         break;
       }
+    }
+    if (a.work && lane == 0) {
+      atomicAdd(a.work, (unsigned long long)iters);
+      atomicAdd(a.work + 1, (unsigned long long)evals);
     }
     // ---- epilogues
     if (a.mode == MODE_RAW || a.mode == MODE_KNN) {

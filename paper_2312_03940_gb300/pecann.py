@@ -34,7 +34,8 @@ class PecannParams(ctypes.Structure):
                 ("max_dep_beam", ctypes.c_int32), ("density", ctypes.c_int32),
                 ("normalize_density", ctypes.c_int32), ("center", ctypes.c_int32), ("rho_min", ctypes.c_float),
                 ("delta_min", ctypes.c_float), ("n_clusters", ctypes.c_int32), ("hash_slots", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("collect_work", ctypes.c_int32), ("build_passes", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class PecannDataset(ctypes.Structure):
@@ -164,6 +165,13 @@ def pecann_workspace_size(ds: Dataset, p: PecannParams) -> int:
     b = ctypes.c_size_t(0)
     _check(load_library().pecann_workspace_size(ds.ref, ctypes.byref(p), ctypes.byref(b)))
     return b.value
+
+
+def work_counters(ws: torch.Tensor):
+    """(expansions, distance evaluations) left in the workspace by the last
+    pecann_search / pecann_density call made with collect_work = 1."""
+    v = ws[80:96].cpu().view(torch.int64)
+    return int(v[0]), int(v[1])
 
 
 def workspace(ds: Dataset, p: PecannParams) -> torch.Tensor:

@@ -44,8 +44,8 @@ def test_params_default_and_strings(lib):
 
 
 def test_struct_layout_matches_header(lib):
-    # pecann_params: 20 four-byte fields, then a uint64 -> 88 bytes
-    assert ctypes.sizeof(pc.PecannParams) == 88
+    # pecann_params: 22 four-byte fields, then a uint64 -> 96 bytes
+    assert ctypes.sizeof(pc.PecannParams) == 96
     assert ctypes.sizeof(pc.PecannDataset) == 48
 
 

@@ -100,12 +100,15 @@ def test_search_matches_oracle(dtype, d, metric):
             assert (dis[r, :cnt[r]] == od).all(), (L, qq)
 
 
-def test_search_with_start_set():
+@pytest.mark.parametrize("n_start", [20, 700])
+def test_search_with_start_set(n_start):
+    """Start sets smaller and larger than the staging area (the larger one is
+    merged in chunks)."""
     n = 3000
     X, _ = synth.gaussian_mixture(n=n, d=32, components=6, seed=3)
     G = random_graph(n, 16, seed=3)
     P = oracle.Points(X)
-    S = synth.sample_ids(n, 20, seed=4).astype(np.int32)
+    S = synth.sample_ids(n, n_start, seed=4).astype(np.int32)
     q = np.concatenate([S[:5], synth.sample_ids(n, 60, seed=5).astype(np.int32)])  # some queries in S
     ids, dis, cnt = pc.pecann_search(pc.Dataset(t(X)), t(G), t(q), L=40, k=40, start=t(S))
     ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy()
@@ -116,8 +119,9 @@ def test_search_with_start_set():
 
 # ---------------------------------------------------------------- graph build
 
-@pytest.mark.parametrize("kind", ["f32", "u8", "ip"])
-def test_build_graph_matches_oracle(kind):
+@pytest.mark.parametrize("kind,passes,n_start", [("f32", 1, 12), ("u8", 1, 12), ("ip", 1, 12), ("u8", 2, 12),
+                                                  ("f32", 2, 300)])
+def test_build_graph_matches_oracle(kind, passes, n_start):
     n = 3000
     if kind == "u8":
         X, _ = synth.u8_mixture(n=n, d=128, components=12, seed=11)
@@ -129,11 +133,12 @@ def test_build_graph_matches_oracle(kind):
             X = (X / np.linalg.norm(X, axis=1, keepdims=True)).astype(np.float32)
             metric = pc.IP
     order = synth.insertion_order(n, seed=13)
-    p = pc.params(R=24, L_build=48, alpha=1.2, n_start=12, batch_frac=0.02)
+    p = pc.params(R=24, L_build=48, alpha=1.2, n_start=n_start, batch_frac=0.02, build_passes=passes)
     ds = pc.Dataset(t(X), metric=metric)
     G, deg = pc.pecann_build_graph(ds, p, order=t(order))
     G = G.cpu().numpy()
-    Go = oracle.build_graph(oracle.Points(X, metric=metric), R=24, L=48, alpha=1.2, perm=order, n_start=12)
+    Go = oracle.build_graph(oracle.Points(X, metric=metric), R=24, L=48, alpha=1.2, perm=order, n_start=n_start,
+                            passes=passes)
     assert (G == Go).all()
     assert (deg.cpu().numpy() == (Go >= 0).sum(1)).all()
 
