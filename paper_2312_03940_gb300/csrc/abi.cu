@@ -93,8 +93,11 @@ static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv) {
 static int log2_hash(const pecann_params* p, int Lw) {
   int slots = p->hash_slots;
   if (slots <= 0) {
-    slots = 16 * Lw;
-    slots = std::max(2048, std::min(slots, 16384));
+    // 8 slots per beam entry: at a beam of 128 this keeps a warp's shared
+    // memory near 6 KB (32 warps per SM); the filter forgets some ids, which
+    // costs repeated distances but never changes a result
+    slots = 8 * Lw;
+    slots = std::max(512, std::min(slots, 16384));
   }
   int l = 0;
   while ((1 << l) < slots) l++;

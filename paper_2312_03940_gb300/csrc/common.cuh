@@ -77,6 +77,11 @@ __device__ __forceinline__ uint4 ldg_nc(const uint4* p) {
 
 __device__ __forceinline__ uint4 ldg_l1(const uint4* p) { return __ldg(p); }
 
+// Start moving a line into L2 without waiting for it (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // ----------------------------------------------------------------- row chunks
 
 // Load the CPL chunks of a row owned by group lane g (chunk g + W*t).

@@ -117,6 +117,14 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
   constexpr int GR = 32 / W;
   constexpr int UNR = CPL >= 4 ? 1 : (CPL == 1 ? 4 : 2);
   const int g = lane / W, gl = lane % W;
+  if (nc > GR * UNR) {
+    // rows beyond the first batch: start their fetch now, so the later
+    // batches find them in L2 instead of waiting a full DRAM round trip each
+    for (int c = GR * UNR + lane; c < nc; c += 32) {
+      const uint8_t* r = a.X + (int64_t)w.cids[c] * a.row_bytes;
+      for (int64_t off = 0; off < a.row_bytes; off += 128) prefetch_l2(r + off);
+    }
+  }
   for (int c0 = 0; c0 < nc; c0 += GR * UNR) {
     uint4 r[UNR][CPL];
 #pragma unroll
@@ -218,13 +226,20 @@ __device__ int merge_cands(WarpSmem& w, int& nb, int Lw, int nc, int& cursor, in
   return m2;
 }
 
-__device__ __forceinline__ int find_unvisited(const uint64_t* beam, int nb, int from, int lane) {
+// First unvisited beam entry at or after `from` (-1 if none); *next gets the
+// second one when it lies in the same 32-entry window (else -1).
+__device__ __forceinline__ int find_unvisited(const uint64_t* beam, int nb, int from, int lane, int* next) {
   for (int b = from; b < nb; b += 32) {
     int i = b + lane;
     bool u = i < nb && !(beam[i] & VFLAG);
     unsigned m = __ballot_sync(FULL, u);
-    if (m) return b + __ffs(m) - 1;
+    if (m) {
+      unsigned rest = m & (m - 1);
+      *next = rest ? b + __ffs(rest) - 1 : -1;
+      return b + __ffs(m) - 1;
+    }
   }
+  *next = -1;
   return -1;
 }
 
@@ -290,7 +305,7 @@ __device__ void density_from_beam(const uint64_t* beam, int k, int metric, int f
 }
 
 template <int DT, int METRIC, int W, int CPL>
-__global__ void __launch_bounds__(256) k_search(SearchArgs a) {
+__global__ void __launch_bounds__(256, 5) k_search(SearchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpSmem w = carve(smem + (size_t)wib * a.warp_bytes, a);
@@ -339,9 +354,13 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a) {
     }
     for (;;) {
       // p* <- argmin over L \ V
-      int pos = find_unvisited(w.beam, nb, cursor, lane);
+      int next;
+      int pos = find_unvisited(w.beam, nb, cursor, lane, &next);
       if (pos < 0) break;
       uint64_t e = w.beam[pos];
+      // the runner-up is usually the next point popped: fetch its out-list early
+      if (next >= 0 && lane < (a.R * 4 + 127) / 128)
+        prefetch_l2(a.G + (int64_t)key_id(w.beam[next]) * a.R + lane * 32);
       __syncwarp();
       if (lane == 0) w.beam[pos] = e | VFLAG;  // V <- V u {p*}
       __syncwarp();
