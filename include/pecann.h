@@ -238,6 +238,32 @@ PECANN_API pecann_status pecann_cluster(int64_t n, const float* d_density, const
                              const float* d_dep_dist, const pecann_params* p, int32_t* d_labels,
                              int64_t* h_n_clusters, void* ws, size_t ws_bytes, void* stream);
 
+/* Largest point set pecann_density_noalloc accepts. */
+#define PECANN_NOALLOC_MAX_POINTS (1 << 20)
+
+/*
+ * pecann_density without a workspace, for callers that cannot allocate GPU
+ * memory (for example code running under an external memory manager that
+ * owns every device byte, or a loop that must never take the allocator's
+ * lock). The paper has no counterpart: this is a packaging of
+ * pecann_density, with the same arguments minus the workspace and the same
+ * results, element for element.
+ * Its scratch (about 8 MiB: a fallback list and a density copy for up to
+ * PECANN_NOALLOC_MAX_POINTS points) is one fixed device array inside the
+ * library, present on every GPU that loads the library until the process
+ * exits. The call allocates nothing; n > PECANN_NOALLOC_MAX_POINTS returns
+ * PECANN_EINVAL. The first call on each device looks the array's device
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. Each
+ * call clears what must start at zero; the rest keeps the previous call's
+ * contents. Asynchronous on `stream`, like pecann_density.
+ */
+PECANN_API pecann_status pecann_density_noalloc(const pecann_dataset* ds, const int32_t* d_graph,
+                                                const pecann_params* p, int32_t* d_knn_ids,
+                                                float* d_knn_dist, float* d_density,
+                                                float* d_rank_key, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,7 +47,9 @@ class PecannDataset(ctypes.Structure):
 EXPORTS = ["pecann_params_default", "pecann_status_string", "pecann_last_error", "pecann_version",
            "pecann_kernel_launches",
            "pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
-           "pecann_dependent_points", "pecann_cluster"]
+           "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc"]
+
+NOALLOC_MAX_POINTS = 1 << 20
 
 _lib = None
 
@@ -85,8 +87,9 @@ def load_library(path: str | None = None):
     lib.pecann_density.argtypes = [D, vp, P, vp, vp, vp, vp, vp, sz, vp]
     lib.pecann_dependent_points.argtypes = [D, vp, P, vp, vp, vp, vp, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.pecann_cluster.argtypes = [i64, vp, vp, vp, P, vp, ctypes.POINTER(i64), vp, sz, vp]
+    lib.pecann_density_noalloc.argtypes = [D, vp, P, vp, vp, vp, vp, vp]
     for f in ["pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
-              "pecann_dependent_points", "pecann_cluster"]:
+              "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc"]:
         getattr(lib, f).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -227,6 +230,25 @@ def pecann_density(ds: Dataset, graph: torch.Tensor, p: PecannParams, ws: torch.
     _check(load_library().pecann_density(ds.ref, _ptr(graph), ctypes.byref(p), _ptr(out["knn_ids"]),
                                          _ptr(out["knn_dist"]), _ptr(out["density"]), _ptr(out["rank_key"]),
                                          _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def pecann_density_noalloc(ds: Dataset, graph: torch.Tensor, p: PecannParams, stream=None,
+                           out: dict | None = None):
+    """pecann_density for callers that cannot allocate GPU memory: no
+    workspace; the library's fixed scratch array serves (n <= 2^20, and calls
+    that overlap on the GPU must be serialised by the caller). Outputs are
+    still allocated here unless `out` provides them."""
+    _cuda(graph, "graph", torch.int32)
+    dev = ds.X.device
+    if out is None:
+        out = dict(knn_ids=torch.empty((ds.n, p.k), dtype=torch.int32, device=dev),
+                   knn_dist=torch.empty((ds.n, p.k), dtype=torch.float32, device=dev),
+                   density=torch.empty(ds.n, dtype=torch.float32, device=dev),
+                   rank_key=torch.empty(ds.n, dtype=torch.float32, device=dev))
+    _check(load_library().pecann_density_noalloc(ds.ref, _ptr(graph), ctypes.byref(p), _ptr(out["knn_ids"]),
+                                                 _ptr(out["knn_dist"]), _ptr(out["density"]),
+                                                 _ptr(out["rank_key"]), _stream(stream)))
     return out
 
 
