@@ -63,7 +63,7 @@ struct WsHeader {
   int32_t counts[14];
   unsigned long long gmax;
   unsigned long long roots;
-  unsigned long long work[2];  // byte offset 80: expansions, distance evaluations
+  unsigned long long work[3];  // byte offset 80: expansions, distance evaluations, beam insertions
 };
 static const size_t HDR = 256;
 

@@ -2,6 +2,7 @@
 // over the k-NN lists, the global maximum, compaction of the unfinished
 // points, the exact brute-force tail, and the normalised density pass.
 #include "common.cuh"
+#include "dispatch.cuh"
 #include "internal.h"
 
 namespace pecann {
@@ -146,33 +147,10 @@ cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int
   Layout L;
   if (!pick_layout(dv.dtype, dv.metric, dv.d, &L)) return cudaErrorNotSupported;
   k_fill_u64<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(best, m, KEY_NONE); note_launch();
-  cudaError_t e = cudaErrorNotSupported;
-#define PECANN_DINST(DT, MET)                                                            \
-  if (L.W == 8)                                                                          \
-    e = launch_dep_bf_inst<DT, MET, 8, 1>(dv, d_list, m, rank_key, best, st);            \
-  else if (L.W == 16)                                                                    \
-    e = launch_dep_bf_inst<DT, MET, 16, 1>(dv, d_list, m, rank_key, best, st);           \
-  else if (L.CPL == 1)                                                                   \
-    e = launch_dep_bf_inst<DT, MET, 32, 1>(dv, d_list, m, rank_key, best, st);           \
-  else if (L.CPL == 2)                                                                   \
-    e = launch_dep_bf_inst<DT, MET, 32, 2>(dv, d_list, m, rank_key, best, st);           \
-  else if (L.CPL == 3)                                                                   \
-    e = launch_dep_bf_inst<DT, MET, 32, 3>(dv, d_list, m, rank_key, best, st);           \
-  else if (L.CPL == 4)                                                                   \
-    e = launch_dep_bf_inst<DT, MET, 32, 4>(dv, d_list, m, rank_key, best, st);           \
-  else                                                                                   \
-    e = launch_dep_bf_inst<DT, MET, 32, 8>(dv, d_list, m, rank_key, best, st);
-  if (dv.dtype == DT_F32 && dv.metric == MET_L2) {
-    PECANN_DINST(DT_F32, MET_L2)
-  } else if (dv.dtype == DT_F32 && dv.metric == MET_IP) {
-    PECANN_DINST(DT_F32, MET_IP)
-  } else if (dv.dtype == DT_U8) {
-    if (L.W == 8)
-      e = launch_dep_bf_inst<DT_U8, MET_L2, 8, 1>(dv, d_list, m, rank_key, best, st);
-    else
-      e = launch_dep_bf_inst<DT_U8, MET_L2, 16, 1>(dv, d_list, m, rank_key, best, st);
-  }
-#undef PECANN_DINST
+  cudaError_t e = dispatch_layout(dv, [&](auto dt, auto met, auto wv, auto cpl) -> cudaError_t {
+    return launch_dep_bf_inst<decltype(dt)::value, decltype(met)::value, decltype(wv)::value,
+                              decltype(cpl)::value>(dv, d_list, m, rank_key, best, st);
+  });
   if (e != cudaSuccess) return e;
   k_dep_bf_finish<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(d_list, m, best, dv.metric, lam, delta); note_launch();
   return cudaGetLastError();

@@ -26,7 +26,8 @@ struct SearchArgs {
   const int32_t* S;   // start set, or NULL for {query}
   int nS;
   int Lw;             // beam width
-  int log2h;          // seen-filter slots = 1 << log2h
+  int log2h;          // seen-filter size: (1 << log2h) 32-bit words
+  int hash16;         // set by launch_search: the filter holds 2 << log2h 16-bit tags
   int stage;          // candidate staging entries per warp (>= max(R, nS))
   int vcap;           // BUILD: visited points kept
   int mode;

@@ -1,0 +1,301 @@
+// Device helpers of the beam-search kernels (search.cu): per-warp
+// shared-memory carving, admission of candidate ids through the seen-filter,
+// candidate scoring, the merge into the sorted beam, visit recording and the
+// density epilogue.
+#pragma once
+
+#include <float.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pecann {
+
+struct WarpSmem {
+  uint64_t* beam;
+  uint64_t* ckeys;
+  uint64_t* ss;
+  uint64_t* vis;
+  int32_t* hash;
+  int32_t* cids;
+};
+
+inline int search_warp_bytes_impl(int Lw, int log2h, int stage, int vcap, bool build) {
+  size_t b = (size_t)Lw * 8 + (size_t)stage * 16 + (build ? (size_t)vcap * 8 : 0) +
+             ((size_t)1 << log2h) * 4 + (size_t)stage * 4;
+  return (int)((b + 15) & ~(size_t)15);
+}
+
+__device__ __forceinline__ WarpSmem carve(uint8_t* base, const SearchArgs& a) {
+  WarpSmem w;
+  w.beam = reinterpret_cast<uint64_t*>(base);
+  w.ckeys = w.beam + a.Lw;
+  w.ss = w.ckeys + a.stage;
+  w.vis = w.ss + a.stage;
+  w.hash = reinterpret_cast<int32_t*>(w.vis + (a.mode == MODE_BUILD ? a.vcap : 0));
+  w.cids = w.hash + (1 << a.log2h);
+  return w;
+}
+
+// Admit id y as a new candidate unless it is padding, the query or already
+// evaluated (as far as the filter remembers). Collective over the warp.
+__device__ __forceinline__ int admit(const SearchArgs& a, WarpSmem& w, int32_t y, int32_t q, int nc,
+                                     int lane) {
+  bool take = false;
+  if (y >= 0) {
+    if (y >= a.n) {
+      set_error(a.err, ERR_BAD_ID);
+    } else if (y != q) {
+      if (a.hash16) {
+        // twice the slots in the same bytes: slot = low id bits, tag = the
+        // remaining high bits, so a match still means exactly this id
+        uint16_t* h16 = reinterpret_cast<uint16_t*>(w.hash);
+        const uint32_t s = (uint32_t)y & ((2u << a.log2h) - 1);
+        const uint16_t tag = (uint16_t)((uint32_t)y >> (a.log2h + 1));
+        if (h16[s] != tag) {
+          h16[s] = tag;
+          take = true;
+        }
+      } else {
+        uint32_t s = hash_slot(y, a.log2h);
+        if (w.hash[s] != y) {
+          w.hash[s] = y;
+          take = true;
+        }
+      }
+    }
+  }
+  unsigned m = __ballot_sync(FULL, take);
+  if (take) w.cids[nc + __popc(m & lanemask_lt())] = y;
+  return nc + __popc(m);
+}
+
+// Candidate ids from the out-list of p.
+__device__ __forceinline__ int gather_out(const SearchArgs& a, WarpSmem& w, int32_t p, int32_t q,
+                                          int lane) {
+  const int32_t* row = a.G + (int64_t)p * a.R;
+  int nc = 0;
+  for (int b = 0; b < a.R; b += 32) {
+    int idx = b + lane;
+    int32_t y = idx < a.R ? __ldg(row + idx) : -1;
+    nc = admit(a, w, y, q, nc, lane);
+  }
+  __syncwarp();
+  return nc;
+}
+
+// Candidate ids from the start points S[s0 .. s0 + stage); *q_in_s is set
+// when the query itself is one of them.
+__device__ __forceinline__ int gather_start(const SearchArgs& a, WarpSmem& w, int32_t q, int s0, int lane,
+                                            bool* q_in_s) {
+  int nc = 0;
+  bool has_q = false;
+  const int s1 = min(a.nS, s0 + a.stage);
+  for (int b = s0; b < s1; b += 32) {
+    int idx = b + lane;
+    int32_t y = idx < s1 ? __ldg(a.S + idx) : -1;
+    has_q |= __any_sync(FULL, y == q);
+    nc = admit(a, w, y, q, nc, lane);
+  }
+  __syncwarp();
+  *q_in_s |= has_q;
+  return nc;
+}
+
+// Keys (canonical distance to the query, id) of the staged candidates.
+template <int DT, int METRIC, int W, int CPL>
+__device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int nc,
+                                           const uint4 (&qv)[CPL], int lane) {
+  constexpr int GR = 32 / W;
+  constexpr int UNR = CPL >= 4 ? 1 : (CPL == 1 ? 4 : 2);
+  const int g = lane / W, gl = lane % W;
+  if (nc > GR * UNR) {
+    // rows beyond the first batch: start their fetch now, so the later
+    // batches find them in L2 instead of waiting a full DRAM round trip each
+    for (int c = GR * UNR + lane; c < nc; c += 32) {
+      const uint8_t* r = a.X + (int64_t)w.cids[c] * a.row_bytes;
+      for (int64_t off = 0; off < a.row_bytes; off += 128) prefetch_l2(r + off);
+    }
+  }
+  for (int c0 = 0; c0 < nc; c0 += GR * UNR) {
+    uint4 r[UNR][CPL];
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      int c = c0 + u * GR + g;
+      if (c < nc) {
+        load_row<W, CPL, true>(a.X + (int64_t)w.cids[c] * a.row_bytes, gl, a.C, r[u]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < CPL; t++) r[u][t] = make_uint4(0, 0, 0, 0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      float dv = group_dis<DT, METRIC, W, CPL>(qv, r[u]);
+      int c = c0 + u * GR + g;
+      if (gl == 0 && c < nc) w.ckeys[c] = make_key(dv, w.cids[c]);
+    }
+  }
+  __syncwarp();
+}
+
+// Number of entries of the sorted clean keys s[0..m) below x.
+__device__ __forceinline__ int count_below(const uint64_t* s, int m, uint64_t x) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (s[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Merge the staged candidate keys into the beam (keep the Lw smallest keys,
+// no duplicates). Returns the number of keys merged. Collective.
+__device__ __forceinline__ int merge_cands(WarpSmem& w, int& nb, int Lw, int nc, int& cursor, int lane) {
+  // 1) drop candidates no better than the current worst entry of a full beam
+  uint64_t worst = nb >= Lw ? key_clean(w.beam[Lw - 1]) : KEY_NONE;
+  int m = 0;
+  for (int b = 0; b < nc; b += 32) {
+    int i = b + lane;
+    uint64_t kk = i < nc ? w.ckeys[i] : KEY_NONE;
+    bool keep = i < nc && kk < worst;
+    unsigned bm = __ballot_sync(FULL, keep);
+    __syncwarp();
+    if (keep) w.ckeys[m + __popc(bm & lanemask_lt())] = kk;
+    m += __popc(bm);
+    __syncwarp();
+  }
+  if (m == 0) return 0;
+  // 2) duplicates: of an earlier survivor, or of a beam entry
+  for (int i = lane; i < m; i += 32) {
+    uint64_t kk = w.ckeys[i];
+    int lb = lower_bound_key(w.beam, nb, kk);
+    bool dup = lb < nb && key_clean(w.beam[lb]) == kk;
+    for (int j = 0; j < i && !dup; j++) dup = w.ckeys[j] == kk;
+    w.cids[i] = dup ? 0 : 1;
+  }
+  __syncwarp();
+  // 3) sort the survivors by rank counting
+  int m2 = 0;
+  for (int i = 0; i < m; i++) m2 += w.cids[i];
+  for (int i = lane; i < m; i += 32) {
+    if (!w.cids[i]) continue;
+    uint64_t kk = w.ckeys[i];
+    int rank = 0;
+    for (int j = 0; j < m; j++) rank += (w.cids[j] && w.ckeys[j] < kk);
+    w.ss[rank] = kk;
+  }
+  __syncwarp();
+  if (m2 == 0) return 0;
+  // 4) insertion points in the old beam
+  for (int r = lane; r < m2; r += 32) w.cids[r] = lower_bound_key(w.beam, nb, w.ss[r]);
+  __syncwarp();
+  const int p0 = w.cids[0];
+  // 5) shift the beam entries at or after p0, from the back, in place
+  for (int hi = nb - 1; hi >= p0; hi -= 32) {
+    int idx = hi - lane;
+    uint64_t e = 0;
+    int dst = Lw;
+    if (idx >= p0) {
+      e = w.beam[idx];
+      dst = idx + count_below(w.ss, m2, key_clean(e));
+    }
+    __syncwarp();
+    if (dst < Lw) w.beam[dst] = e;
+    __syncwarp();
+  }
+  // 6) place the survivors
+  for (int r = lane; r < m2; r += 32) {
+    int dst = r + w.cids[r];
+    if (dst < Lw) w.beam[dst] = w.ss[r];
+  }
+  __syncwarp();
+  nb = min(Lw, nb + m2);
+  if (p0 < cursor) cursor = p0;
+  return m2;
+}
+
+// First unvisited beam entry at or after `from` (-1 if none); *next gets the
+// second one when it lies in the same 32-entry window (else -1).
+__device__ __forceinline__ int find_unvisited(const uint64_t* beam, int nb, int from, int lane, int* next) {
+  for (int b = from; b < nb; b += 32) {
+    int i = b + lane;
+    bool u = i < nb && !(beam[i] & VFLAG);
+    unsigned m = __ballot_sync(FULL, u);
+    if (m) {
+      unsigned rest = m & (m - 1);
+      *next = rest ? b + __ffs(rest) - 1 : -1;
+      return b + __ffs(m) - 1;
+    }
+  }
+  *next = -1;
+  return -1;
+}
+
+// Keep the vcap closest expanded points (build searches).
+__device__ __forceinline__ void record_visit(WarpSmem& w, int& nv, int vcap, uint64_t e, int lane) {
+  if (nv < vcap) {
+    if (lane == 0) w.vis[nv] = e;
+    nv++;
+  } else {
+    uint64_t mx = 0;
+    int mi = -1;
+    for (int i = lane; i < vcap; i += 32)
+      if (w.vis[i] > mx) {
+        mx = w.vis[i];
+        mi = i;
+      }
+    uint64_t gm = mx;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      uint64_t o = __shfl_xor_sync(FULL, gm, off);
+      gm = o > gm ? o : gm;
+    }
+    if (e < gm && mi >= 0 && mx == gm) w.vis[mi] = e;
+  }
+  __syncwarp();
+}
+
+// Density of a point from its first k beam entries (Sec. 4.2, Appendix A).
+// Separate rounded operations, as the definition reads.
+__device__ __forceinline__ void density_from_beam(const uint64_t* beam, int k, int metric, int fn, float* rho,
+                                  float* key) {
+  if (fn == PECANN_DENS_KTH) {
+    float D = out_dist(key_dis(key_clean(beam[k - 1])), metric);
+    float r = __fdiv_rn(1.0f, D);
+    *rho = r;
+    *key = r;
+    return;
+  }
+  float s = 0.0f;
+  for (int t = 0; t < k; t++) {
+    float dis = key_dis(key_clean(beam[t]));
+    float D = out_dist(dis, metric);
+    float d2 = metric == MET_L2 ? dis : __fmul_rn(D, D);
+    if (fn == PECANN_DENS_EXPSUM)
+      s = __fadd_rn(s, d2);
+    else if (fn == PECANN_DENS_SUMEXP)
+      s = __fadd_rn(s, expf(-d2));
+    else
+      s = __fadd_rn(s, D);
+  }
+  if (fn == PECANN_DENS_EXPSUM) {
+    float kk = __fdiv_rn(-s, (float)k);
+    *key = kk;
+    *rho = expf(kk);
+  } else if (fn == PECANN_DENS_SUMEXP) {
+    float r = __fdiv_rn(s, (float)k);
+    *rho = r;
+    *key = r;
+  } else {
+    *rho = -s;
+    *key = -s;
+  }
+}
+
+
+}  // namespace pecann

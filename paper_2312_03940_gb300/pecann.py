@@ -171,10 +171,10 @@ def pecann_workspace_size(ds: Dataset, p: PecannParams) -> int:
 
 
 def work_counters(ws: torch.Tensor):
-    """(expansions, distance evaluations) left in the workspace by the last
+    """(expansions, distance evaluations, beam insertions) left in the workspace by the last
     pecann_search / pecann_density call made with collect_work = 1."""
-    v = ws[80:96].cpu().view(torch.int64)
-    return int(v[0]), int(v[1])
+    v = ws[80:104].cpu().view(torch.int64)
+    return int(v[0]), int(v[1]), int(v[2])
 
 
 def workspace(ds: Dataset, p: PecannParams) -> torch.Tensor:
