@@ -31,6 +31,15 @@
  *  - Point rows are n x d, row-major, contiguous, 16-byte aligned. d must be
  *    a multiple of 4 (FP32), 8 (BF16) or 16 (U8, FP8). U8 supports the L2
  *    metric with d <= 256 (so that every distance is an exact integer in FP32).
+ *  - Reduced-precision traversal: a BF16 dataset must also give data_f32,
+ *    the same points in FP32. Graph searches walk the BF16 rows (FP32
+ *    accumulation); every distance that leaves the library (k-NN lists,
+ *    densities, dependent distances) is recomputed exactly on the FP32 rows
+ *    for the candidates the traversal found: the k-NN search hands its
+ *    rerank_k best points, each dependent round its first 32 points ranked
+ *    above the query. Graph builds, brute-force fallbacks and the
+ *    brute-force tail use the FP32 rows. FP8 traversal has no kernel yet
+ *    (PECANN_EUNSUPPORTED).
  *  - Distances: the library orders points by the FP32 "dissimilarity" dis --
  *    the squared Euclidean distance (L2) or 1 - <x, y> (IP, unit-norm rows) --
  *    summed in one fixed order: 4-element chunk c of a row is accumulated with
@@ -110,7 +119,8 @@ typedef struct {
                                 byte offset 80 of the workspace                          */
   int32_t build_passes;      /* 1, or 2: a first insertion pass pruning with alpha = 1,
                                 then a second over all points with alpha   build              */
-  int32_t reserved1;
+  int32_t rerank_k;          /* BF16 traversal: candidates per point re-scored in FP32
+                                (0: min(L_search, 4k); must be >= k)         density          */
   uint64_t seed;             /* insertion order when none is given         build              */
 } pecann_params;
 
@@ -131,7 +141,7 @@ typedef struct {
    alpha 1.1, n_start 16, batch_frac 0.02, visit_cap 0, dep_threshold 300,
    max_dep_rounds 30, max_dep_beam 8192, kth density, no normalisation,
    product center, rho_min 0, delta_min 0, n_clusters 1, hash_slots 0,
-   collect_work 0, build_passes 1, seed 0. */
+   collect_work 0, build_passes 1, rerank_k 0, seed 0. */
 PECANN_API void pecann_params_default(pecann_params* p);
 
 /* Static string for a status code. */

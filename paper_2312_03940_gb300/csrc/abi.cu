@@ -69,7 +69,11 @@ static const size_t HDR = 256;
 
 static int elem_bytes(int dtype) { return dtype == DT_F32 ? 4 : (dtype == DT_BF16 ? 2 : 1); }
 
-static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv) {
+static bool is_reduced(int dtype) { return dtype == DT_BF16 || dtype == DT_FP8; }
+
+// Checks the dataset and fills the view of its rows; f32 (optional) gets the
+// FP32 rows: the same view for FP32 / U8 data, data_f32 for BF16 / FP8.
+static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataView* f32 = nullptr) {
   if (!ds || !ds->data) return set_last_error("dataset or data pointer is NULL"), PECANN_EINVAL;
   if (ds->n < 2 || ds->n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
   if (ds->dtype < 0 || ds->dtype > 3 || ds->metric < 0 || ds->metric > 1)
@@ -77,9 +81,13 @@ static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv) {
   int epc = 16 / elem_bytes(ds->dtype);
   if (ds->d <= 0 || ds->d % epc) return set_last_error("d must be a positive multiple of 16 bytes / element size"), PECANN_EINVAL;
   if (((uintptr_t)ds->data) & 15) return set_last_error("rows must be 16-byte aligned"), PECANN_EINVAL;
+  if (is_reduced(ds->dtype) && (!ds->data_f32 || (((uintptr_t)ds->data_f32) & 15)))
+    return set_last_error("BF16 / FP8 data needs 16-byte aligned FP32 rows in data_f32"), PECANN_EINVAL;
   Layout L;
   if (!pick_layout(ds->dtype, ds->metric, ds->d, &L))
     return set_last_error("no kernel for this dtype / metric / d"), PECANN_EUNSUPPORTED;
+  if (is_reduced(ds->dtype) && !pick_layout(DT_F32, ds->metric, ds->d, &L))
+    return set_last_error("no FP32 re-rank kernel for this d"), PECANN_EUNSUPPORTED;
   dv->X = (const uint8_t*)ds->data;
   dv->n = ds->n;
   dv->d = ds->d;
@@ -87,7 +95,23 @@ static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv) {
   dv->metric = ds->metric;
   dv->row_bytes = (int64_t)ds->d * elem_bytes(ds->dtype);
   dv->C = (int)(dv->row_bytes / 16);
+  if (f32) {
+    *f32 = *dv;
+    if (is_reduced(ds->dtype)) {
+      f32->X = (const uint8_t*)ds->data_f32;
+      f32->dtype = DT_F32;
+      f32->row_bytes = (int64_t)ds->d * 4;
+      f32->C = (int)(f32->row_bytes / 16);
+    }
+  }
   return PECANN_OK;
+}
+
+static const int DEP_RERANK = 32;  // dependent rounds: candidates re-scored per query
+
+static int rerank_k_of(const pecann_params* p) {
+  int K = p->rerank_k > 0 ? p->rerank_k : std::min(p->L_search, 4 * p->k);
+  return std::max(K, p->k);
 }
 
 static int log2_hash(const pecann_params* p, int Lw) {
@@ -139,8 +163,16 @@ static pecann_status check_params(const pecann_params* p, int64_t n) {
 }
 
 // Workspace pieces of each call (bytes after the header).
-static size_t density_bytes(int64_t n) { return 2 * al((size_t)n * 4); }
-static size_t dep_bytes(int64_t n) { return 2 * al((size_t)n * 4) + al((size_t)n * 8); }
+static size_t density_bytes(int64_t n, int reduced_K) {
+  size_t b = 2 * al((size_t)n * 4);
+  if (reduced_K > 0) b += 2 * al((size_t)n * reduced_K * 4) + al((size_t)n * 4);
+  return b;
+}
+static size_t dep_bytes(int64_t n, bool reduced) {
+  size_t b = 2 * al((size_t)n * 4) + al((size_t)n * 8);
+  if (reduced) b += al((size_t)n * DEP_RERANK * 4) + al((size_t)n * 4);
+  return b;
+}
 
 }  // namespace pecann
 
@@ -172,6 +204,7 @@ void pecann_params_default(pecann_params* p) {
   p->hash_slots = 0;
   p->collect_work = 0;
   p->build_passes = 1;
+  p->rerank_k = 0;
   p->seed = 0;
 }
 
@@ -198,8 +231,9 @@ pecann_status pecann_workspace_size(const pecann_dataset* ds, const pecann_param
   if (!ds || !p || !bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
   int64_t n = ds->n;
   if (n < 2) return set_last_error("n out of range"), PECANN_EINVAL;
-  size_t b = density_bytes(n);
-  b = std::max(b, dep_bytes(n));
+  const bool red = is_reduced(ds->dtype);
+  size_t b = density_bytes(n, red ? std::min(std::max(rerank_k_of(p), 1), 8192) : 0);
+  b = std::max(b, dep_bytes(n, red));
   b = std::max(b, cluster_ws_bytes(n));
   if (p->R >= 1 && p->L_build >= 1) {
     int vcap = p->visit_cap > 0 ? p->visit_cap : 2 * p->L_build;
@@ -258,8 +292,8 @@ pecann_status pecann_search(const pecann_dataset* ds, const int32_t* d_graph, in
 
 pecann_status pecann_build_graph(const pecann_dataset* ds, const pecann_params* p, const int32_t* d_order,
                                  int32_t* d_graph, int32_t* d_degree, void* ws, size_t ws_bytes, void* stream) {
-  DataView dv;
-  pecann_status s = check_dataset(ds, &dv);
+  DataView dv0, dv;
+  pecann_status s = check_dataset(ds, &dv0, &dv);  // the build always uses the FP32 (or U8) rows
   if (s) return s;
   if (!p || !d_graph || !ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
   if (p->R < 1 || p->R > 256) return set_last_error("R must be in 1..256"), PECANN_EINVAL;
@@ -287,14 +321,17 @@ pecann_status pecann_build_graph(const pecann_dataset* ds, const pecann_params* 
 pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, const pecann_params* p,
                              int32_t* d_knn_ids, float* d_knn_dist, float* d_density, float* d_rank_key,
                              void* ws, size_t ws_bytes, void* stream) {
-  DataView dv;
-  pecann_status s = check_dataset(ds, &dv);
+  DataView dv, fv;
+  pecann_status s = check_dataset(ds, &dv, &fv);
   if (s) return s;
   if ((s = check_params(p, dv.n))) return s;
   if (!d_graph || !d_knn_ids || !d_knn_dist || !d_density || !d_rank_key || !ws)
     return set_last_error("NULL pointer"), PECANN_EINVAL;
   if (p->density < 0 || p->density > 3) return set_last_error("bad density function"), PECANN_EINVAL;
-  if (ws_bytes < HDR + density_bytes(dv.n)) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  const bool reduced = is_reduced(dv.dtype);
+  const int K = reduced ? rerank_k_of(p) : 0;
+  if (reduced && K > p->L_search) return set_last_error("rerank_k must be in k..L_search"), PECANN_EINVAL;
+  if (ws_bytes < HDR + density_bytes(dv.n, K)) return set_last_error("workspace too small"), PECANN_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
   WsHeader* h = (WsHeader*)ws;
   uint8_t* w = (uint8_t*)ws + HDR;
@@ -328,9 +365,25 @@ pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, c
   a.fb_cnt = &h->counts[0];
   a.err = &h->err;
   a.work = p->collect_work ? h->work : nullptr;
-  if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
+  if (reduced) {
+    // walk the BF16 rows, keep the K best candidates, re-rank them in FP32
+    int32_t* rr_ids = (int32_t*)(w + 2 * al((size_t)dv.n * 4));
+    float* rr_dis = (float*)((uint8_t*)rr_ids + al((size_t)dv.n * K * 4));
+    int32_t* rr_cnt = (int32_t*)((uint8_t*)rr_dis + al((size_t)dv.n * K * 4));
+    a.mode = MODE_RAW;
+    a.k = K;
+    a.out_ids = rr_ids;
+    a.out_dis = rr_dis;
+    a.out_cnt = rr_cnt;
+    if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
+    e = launch_rerank_knn(fv, rr_ids, rr_cnt, K, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key, p->density,
+                          fb_list, &h->counts[0], st);
+    if ((s = cuda_status(e, "FP32 re-rank"))) return s;
+  } else {
+    if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
+  }
   // points whose search returned fewer than k: exact k-NN by brute force
-  e = launch_bruteforce_knn(dv, fb_list, &h->counts[0], dv.n, p->k, d_knn_ids, d_knn_dist, d_density,
+  e = launch_bruteforce_knn(fv, fb_list, &h->counts[0], dv.n, p->k, d_knn_ids, d_knn_dist, d_density,
                             d_rank_key, p->density, &h->err, st);
   if ((s = cuda_status(e, "brute-force k-NN"))) return s;
   if (p->normalize_density) {
@@ -347,23 +400,26 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
                                       const float* d_rank_key, const int32_t* d_knn_ids, const float* d_knn_dist,
                                       int32_t* d_dep, float* d_dep_dist, int64_t* h_stats, void* ws,
                                       size_t ws_bytes, void* stream) {
-  DataView dv;
-  pecann_status s = check_dataset(ds, &dv);
+  DataView dv, fv;
+  pecann_status s = check_dataset(ds, &dv, &fv);
   if (s) return s;
   if ((s = check_params(p, dv.n))) return s;
   if (!d_graph || !d_rank_key || !d_knn_ids || !d_knn_dist || !d_dep || !d_dep_dist || !ws)
     return set_last_error("NULL pointer"), PECANN_EINVAL;
+  const bool reduced = is_reduced(dv.dtype);
   if (p->L_dep < 1 || p->max_dep_beam < 1 || p->max_dep_beam > 8192 || p->dep_threshold < 0 ||
       p->max_dep_rounds < 0)
     return set_last_error("L_dep, max_dep_beam (<= 8192), dep_threshold or max_dep_rounds out of range"),
            PECANN_EINVAL;
-  if (ws_bytes < HDR + dep_bytes(dv.n)) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  if (ws_bytes < HDR + dep_bytes(dv.n, reduced)) return set_last_error("workspace too small"), PECANN_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
   WsHeader* h = (WsHeader*)ws;
   uint8_t* w = (uint8_t*)ws + HDR;
   int32_t* U0 = (int32_t*)w;
   int32_t* U1 = (int32_t*)(w + al((size_t)dv.n * 4));
   unsigned long long* best = (unsigned long long*)(w + 2 * al((size_t)dv.n * 4));
+  int32_t* rr_ids = (int32_t*)((uint8_t*)best + al((size_t)dv.n * 8));
+  int32_t* rr_cnt = (int32_t*)((uint8_t*)rr_ids + al((size_t)dv.n * DEP_RERANK * 4));
   int64_t stats[64];
   memset(stats, 0, sizeof(stats));
   cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
@@ -404,8 +460,18 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
     a.lam = d_dep;
     a.delta = d_dep_dist;
     a.err = &h->err;
+    if (reduced) {
+      a.mode = MODE_DEPCAND;
+      a.k = DEP_RERANK;
+      a.out_ids = rr_ids;
+      a.out_cnt = rr_cnt;
+    }
     // N_candidates <- FindKnn(i, k_dep); lambda_i <- DPBruteForce(x_i, N_candidates)
     if ((s = cuda_status(launch_search(dv, a, st), "dependent search"))) return s;
+    if (reduced) {
+      e = launch_rerank_dep(fv, U0, nu, rr_ids, rr_cnt, DEP_RERANK, d_dep, d_dep_dist, st);
+      if ((s = cuda_status(e, "FP32 re-rank"))) return s;
+    }
     if ((e = cudaMemsetAsync(&h->counts[2], 0, 4, st)) != cudaSuccess) return cuda_status(e, "memset");
     unsigned ub = (unsigned)std::min<int64_t>((nu + 255) / 256, (int64_t)num_sms() * 8);
     k_compact_unfinished<<<ub, 256, 0, st>>>(U0, nu, d_dep, &h->gmax, U1, &h->counts[2]); note_launch();
@@ -421,7 +487,7 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
   stats[0] = rounds;
   stats[63] = nu;
   // the rest: DPBruteForce over all of P
-  e = launch_dep_bruteforce(dv, U0, nu, d_rank_key, best, d_dep, d_dep_dist, st);
+  e = launch_dep_bruteforce(fv, U0, nu, d_rank_key, best, d_dep, d_dep_dist, st);
   if ((s = cuda_status(e, "brute-force tail"))) return s;
   if ((s = read_err(&h->err, st))) return s;
   if (h_stats) memcpy(h_stats, stats, sizeof(stats));

@@ -28,6 +28,8 @@ cudaError_t dispatch_layout(const DataView& dv, F&& f) {
   };
   if (dv.dtype == DT_F32 && dv.metric == MET_L2) return go(IC<DT_F32>{}, IC<MET_L2>{});
   if (dv.dtype == DT_F32 && dv.metric == MET_IP) return go(IC<DT_F32>{}, IC<MET_IP>{});
+  if (dv.dtype == DT_BF16 && dv.metric == MET_L2) return go(IC<DT_BF16>{}, IC<MET_L2>{});
+  if (dv.dtype == DT_BF16 && dv.metric == MET_IP) return go(IC<DT_BF16>{}, IC<MET_IP>{});
   if (dv.dtype == DT_U8 && dv.metric == MET_L2) {
     if (L.W == 8) return f(IC<DT_U8>{}, IC<MET_L2>{}, IC<8>{}, IC<1>{});
     return f(IC<DT_U8>{}, IC<MET_L2>{}, IC<16>{}, IC<1>{});

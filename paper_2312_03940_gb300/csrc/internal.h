@@ -12,7 +12,7 @@
 namespace pecann {
 
 // Search modes of the beam-search kernel (epilogue selection).
-enum : int { MODE_RAW = 0, MODE_KNN = 1, MODE_DEP = 2, MODE_BUILD = 3 };
+enum : int { MODE_RAW = 0, MODE_KNN = 1, MODE_DEP = 2, MODE_BUILD = 3, MODE_DEPCAND = 4 };
 
 struct SearchArgs {
   const uint8_t* X;   // rows
@@ -87,6 +87,18 @@ cudaError_t launch_bruteforce_knn(const DataView& dv, const int32_t* d_list, con
 cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int64_t m,
                                   const float* rank_key, unsigned long long* best, int32_t* lam,
                                   float* delta, cudaStream_t st);
+
+// Exact FP32 re-rank of candidates found on reduced-precision rows.
+// k-NN: for each point q (0..n-1), the cnt[q] <= K ids cand[q*K ..] are
+// re-scored on the FP32 rows; the k closest (by exact (dis, id)) and the
+// density are written; points with cnt[q] < k are appended to fb_list.
+cudaError_t launch_rerank_knn(const DataView& f32, const int32_t* cand, const int32_t* cnt, int K, int k,
+                              int32_t* knn_ids, float* knn_dist, float* rho, float* rkey, int density_fn,
+                              int32_t* fb_list, int32_t* fb_cnt, cudaStream_t st);
+// Dependent rounds: for each listed query u, the exact closest of its
+// cnt[u] <= K candidates cand[u*K ..] (all ranked above it) becomes lambda.
+cudaError_t launch_rerank_dep(const DataView& f32, const int32_t* list, int64_t m, const int32_t* cand,
+                              const int32_t* cnt, int K, int32_t* lam, float* delta, cudaStream_t st);
 
 int num_sms();
 // Counts the kernels the library launches (reported by pecann_kernel_launches).

@@ -85,6 +85,10 @@ extern "C" pecann_status pecann_density_noalloc(const pecann_dataset* ds, const 
     set_last_error("pecann_density_noalloc: d must fill whole 16-byte chunks and rows must be 16-byte aligned");
     return PECANN_EINVAL;
   }
+  if (ds->dtype == DT_BF16 || ds->dtype == DT_FP8) {
+    set_last_error("pecann_density_noalloc: BF16 / FP8 traversal needs pecann_density (its re-rank scratch)");
+    return PECANN_EUNSUPPORTED;
+  }
   Layout L;
   if (!pick_layout(ds->dtype, ds->metric, ds->d, &L)) {
     set_last_error("pecann_density_noalloc: no kernel for this dtype / metric / d");

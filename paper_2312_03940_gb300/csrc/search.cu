@@ -142,6 +142,24 @@ __global__ void __launch_bounds__(256, 5) k_search(SearchArgs a) {
           density_from_beam(w.beam, a.k, a.metric, a.density_fn, a.rho + q, a.rkey + q);
         }
       }
+    } else if (a.mode == MODE_DEPCAND) {
+      // reduced-precision rounds: hand the first k returned points ranked
+      // above q (in traversal order) to the exact re-rank
+      int cnt = 0;
+      for (int b = 0; b < nb && cnt < a.k; b += 32) {
+        const int t = b + lane;
+        bool ok = false;
+        int32_t id = -1;
+        if (t < nb) {
+          id = key_id(key_clean(w.beam[t]));
+          ok = ranks_above(a.rank_key, id, q);
+        }
+        const unsigned m = __ballot_sync(FULL, ok);
+        const int pos = cnt + __popc(m & lanemask_lt());
+        if (ok && pos < a.k) a.out_ids[qi * a.k + pos] = id;
+        cnt += __popc(m);
+      }
+      if (lane == 0) a.out_cnt[qi] = min(cnt, a.k);
     } else if (a.mode == MODE_DEP) {
       // DPBruteForce over the returned points: the first one ranked above q
       for (int b = 0; b < nb; b += 32) {
