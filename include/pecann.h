@@ -248,6 +248,40 @@ PECANN_API pecann_status pecann_cluster(int64_t n, const float* d_density, const
                              const float* d_dep_dist, const pecann_params* p, int32_t* d_labels,
                              int64_t* h_n_clusters, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * Batched form (many independent FP32 point sets of uneven sizes): the whole
+ * path -- k-NN + density, dependent points, clusters -- for every set, with
+ * one launch per step for all sets. Every set follows exactly the rules of
+ * the single-set calls (its own maximum-rank point, its own doubling test,
+ * its own brute-force tail, its own centers).
+ * Sets: `sets` (HOST array of n_sets <= 4096) of FP32 datasets with one
+ * metric, d <= 1024. Global ids: set s owns ids base[s] .. base[s+1]-1 in
+ * set order (base[0] = 0); every per-point array below is concatenated in
+ * that order and holds set-local ids (graphs: sum(n) x R, -1 padded; k-NN:
+ * sum(n) x k; density, rank key, dep, dep_dist, labels: sum(n)).
+ * pecann_batch_workspace_size: bytes of workspace needed (host call).
+ * pecann_batch_prepare: writes the set table (row and graph pointers, sizes,
+ *   h_n_clusters[s] -- HOST, may be NULL for p->n_clusters) into the
+ *   workspace; blocks until done. Call it once per batch; the workspace then
+ *   belongs to that batch.
+ * pecann_run_batched: one pass of the path over all sets, from the prepared
+ *   workspace and the same `sets`. It issues only kernels, device-to-device
+ *   copies and memsets on `stream` and reads nothing back to the host, so it
+ *   can be captured into a CUDA graph and replayed. The normalised density
+ *   is not offered in batched form (PECANN_EINVAL).
+ */
+PECANN_API pecann_status pecann_batch_workspace_size(int32_t n_sets, const pecann_dataset* sets,
+                                                     const pecann_params* p, size_t* bytes);
+PECANN_API pecann_status pecann_batch_prepare(int32_t n_sets, const pecann_dataset* sets,
+                                              const int32_t* d_graphs, const int32_t* h_n_clusters,
+                                              const pecann_params* p, void* ws, size_t ws_bytes,
+                                              void* stream);
+PECANN_API pecann_status pecann_run_batched(int32_t n_sets, const pecann_dataset* sets,
+                                            const pecann_params* p, int32_t* d_knn_ids,
+                                            float* d_knn_dist, float* d_density, float* d_rank_key,
+                                            int32_t* d_dep, float* d_dep_dist, int32_t* d_labels,
+                                            void* ws, size_t ws_bytes, void* stream);
+
 /* Largest point set pecann_density_noalloc accepts. */
 #define PECANN_NOALLOC_MAX_POINTS (1 << 20)
 

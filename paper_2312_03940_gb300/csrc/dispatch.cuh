@@ -13,6 +13,23 @@ namespace pecann {
 template <int V>
 using IC = std::integral_constant<int, V>;
 
+// f(W, CPL) for the compiled layout of dtype DT that serves L.
+template <int DT, class F>
+cudaError_t dispatch_wc(const Layout& L, F&& f) {
+  if constexpr (DT == DT_U8) {
+    if (L.W == 8) return f(IC<8>{}, IC<1>{});
+    return f(IC<16>{}, IC<1>{});
+  } else {
+    if (L.W == 8) return f(IC<8>{}, IC<1>{});
+    if (L.W == 16) return f(IC<16>{}, IC<1>{});
+    if (L.CPL == 1) return f(IC<32>{}, IC<1>{});
+    if (L.CPL == 2) return f(IC<32>{}, IC<2>{});
+    if (L.CPL == 3) return f(IC<32>{}, IC<3>{});
+    if (L.CPL == 4) return f(IC<32>{}, IC<4>{});
+    return f(IC<32>{}, IC<8>{});
+  }
+}
+
 template <class F>
 cudaError_t dispatch_layout(const DataView& dv, F&& f) {
   Layout L;

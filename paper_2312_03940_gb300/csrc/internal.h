@@ -14,6 +14,16 @@ namespace pecann {
 // Search modes of the beam-search kernel (epilogue selection).
 enum : int { MODE_RAW = 0, MODE_KNN = 1, MODE_DEP = 2, MODE_BUILD = 3, MODE_DEPCAND = 4 };
 
+// One point set of a batched launch (see SearchArgs::sets).
+struct SetDesc {
+  const uint8_t* X;   // rows of the set
+  const int32_t* G;   // its graph (n x R, local ids)
+  int64_t n;
+  int64_t row_bytes;
+  int C;
+  int pad;
+};
+
 struct SearchArgs {
   const uint8_t* X;   // rows
   int64_t row_bytes;  // bytes per row
@@ -53,6 +63,17 @@ struct SearchArgs {
   int32_t* vis_cnt;
   int* err;
   unsigned long long* work;  // optional: [0] expansions, [1] distance evaluations (sums)
+  // batched form (sets != NULL): slots 0..nq-1 (or *nq_dev) are taken from
+  // the device counter *queue; a slot's global point id (queries[slot], or
+  // the slot itself) falls in set s with set_base[s] <= id < set_base[s+1];
+  // outputs are concatenated over the sets and indexed by global id.
+  const SetDesc* sets;
+  const int64_t* set_base;
+  int n_sets;
+  unsigned long long* queue;
+  const int32_t* nq_dev;
+  const int32_t* set_active;  // batched dependent rounds: sets still doubling (NULL: all)
+  int64_t id_base;           // global id of the set's point 0 (0 outside batches)
 };
 
 struct DataView {

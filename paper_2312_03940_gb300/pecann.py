@@ -47,7 +47,8 @@ class PecannDataset(ctypes.Structure):
 EXPORTS = ["pecann_params_default", "pecann_status_string", "pecann_last_error", "pecann_version",
            "pecann_kernel_launches",
            "pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
-           "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc"]
+           "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
+           "pecann_batch_prepare", "pecann_run_batched"]
 
 NOALLOC_MAX_POINTS = 1 << 20
 
@@ -89,7 +90,8 @@ def load_library(path: str | None = None):
     lib.pecann_cluster.argtypes = [i64, vp, vp, vp, P, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.pecann_density_noalloc.argtypes = [D, vp, P, vp, vp, vp, vp, vp]
     for f in ["pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
-              "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc"]:
+              "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
+           "pecann_batch_prepare", "pecann_run_batched"]:
         getattr(lib, f).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -290,3 +292,54 @@ def pecann_cluster(density: torch.Tensor, dep: torch.Tensor, dep_dist: torch.Ten
                                          _ptr(labels), ctypes.byref(nc) if count else None, _ptr(ws),
                                          ws.numel(), _stream(stream)))
     return labels, (nc.value if count else None)
+
+
+class Batch:
+    """Many FP32 point sets run together (pecann_batch_prepare /
+    pecann_run_batched). `datasets` are Dataset objects; `graphs` their graphs
+    (each n_s x R). Outputs are concatenated over the sets in order, with
+    set-local ids; `offsets[s]` is the first row of set s."""
+
+    def __init__(self, datasets, graphs, p: PecannParams, n_clusters=None, stream=None):
+        if not datasets:
+            raise ValueError("no datasets")
+        self.datasets, self.p = list(datasets), p
+        self.n_sets = len(self.datasets)
+        self.sizes = [d.n for d in self.datasets]
+        self.offsets = [0]
+        for n in self.sizes:
+            self.offsets.append(self.offsets[-1] + n)
+        self.N = self.offsets[-1]
+        dev = self.datasets[0].X.device
+        self.graphs = torch.cat([_cuda(g, "graph", torch.int32) for g in graphs]).contiguous()
+        arr = (PecannDataset * self.n_sets)()
+        for i, d in enumerate(self.datasets):
+            arr[i] = d.c
+        self.c_sets = arr
+        b = ctypes.c_size_t(0)
+        lib = load_library()
+        _check(lib.pecann_batch_workspace_size(self.n_sets, arr, ctypes.byref(p), ctypes.byref(b)))
+        self.ws = torch.empty(b.value, dtype=torch.uint8, device=dev)
+        ncl = None
+        if n_clusters is not None:
+            ncl = (ctypes.c_int32 * self.n_sets)(*[int(x) for x in n_clusters])
+        self._ncl = ncl
+        _check(lib.pecann_batch_prepare(self.n_sets, arr, _ptr(self.graphs), ncl, ctypes.byref(p), _ptr(self.ws),
+                                        self.ws.numel(), _stream(stream)))
+        k = p.k
+        self.out = dict(knn_ids=torch.empty((self.N, k), dtype=torch.int32, device=dev),
+                        knn_dist=torch.empty((self.N, k), dtype=torch.float32, device=dev),
+                        density=torch.empty(self.N, dtype=torch.float32, device=dev),
+                        rank_key=torch.empty(self.N, dtype=torch.float32, device=dev),
+                        dep=torch.empty(self.N, dtype=torch.int32, device=dev),
+                        dep_dist=torch.empty(self.N, dtype=torch.float32, device=dev),
+                        labels=torch.empty(self.N, dtype=torch.int32, device=dev))
+
+    def run(self, stream=None):
+        """pecann_run_batched: one pass over all sets (asynchronous; capturable)."""
+        o = self.out
+        _check(load_library().pecann_run_batched(self.n_sets, self.c_sets, ctypes.byref(self.p), _ptr(o["knn_ids"]),
+                                                 _ptr(o["knn_dist"]), _ptr(o["density"]), _ptr(o["rank_key"]),
+                                                 _ptr(o["dep"]), _ptr(o["dep_dist"]), _ptr(o["labels"]),
+                                                 _ptr(self.ws), self.ws.numel(), _stream(stream)))
+        return o
