@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (profiling runs use fewer)")
     ap.add_argument("--quick", action="store_true", help="skip recall, e2e and the CPU baseline")
     ap.add_argument("--subset", type=int, default=SUBSET_N)
+    ap.add_argument("--workload", default="u8-1m", choices=["u8-1m", "batched64", "sphere384", "vmf1024"],
+                    help="u8-1m: the benchmark line; the others print extra report lines")
     return ap.parse_args()
 
 
@@ -388,10 +390,167 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- extra report workloads
+
+def _timed_steps(step, warmup, steps):
+    import torch
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / steps
+
+
+def run_batched64(args):
+    """64 independent FP32 Gaussian mixtures (n log-uniform in [2,000, 200,000],
+    d in {96, 128, 256, 384}, 5-500 components), R=32, L=96, k=8: one batched
+    pass (captured in a CUDA graph, knobs autotuned) vs the same sets run one
+    after another through the single-set calls."""
+    import torch
+
+    from oracle import exact
+    from paper_2312_03940_gb300 import autotune
+    from paper_2312_03940_gb300 import pecann as pc
+    from paper_2312_03940_gb300 import synth
+
+    pc.load_library()
+    sets = synth.batched_sets()
+    comps = [c for _, _, c in sets]
+    p = pc.params(k=8, R=32, L_build=192, L_search=96, L_dep=96, alpha=1.2, build_passes=2, n_clusters=10)
+    dss, graphs = [], []
+    t0 = time.perf_counter()
+    for i, (X, _, _) in enumerate(sets):
+        ds = pc.Dataset(torch.from_numpy(X).cuda())
+        p.n_start = max(16, min(len(X), 8192 * len(X) // 1_000_000))
+        G, _ = pc.pecann_build_graph(ds, p, order=torch.from_numpy(synth.insertion_order(len(X), seed=i)).cuda())
+        dss.append(ds)
+        graphs.append(G)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    batch = pc.Batch(dss, graphs, p, n_clusters=comps)
+    tune = autotune.tune_batch(batch, use_cache=False)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        batch.run(stream=s)
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        batch.run(stream=s)
+    t_graph = _timed_steps(graph.replay, args.warmup, args.steps)
+    t_plain = _timed_steps(batch.run, args.warmup, args.steps)
+    # the same sets one after another through the single-set calls
+    singles = []
+    for i, (ds, G) in enumerate(zip(dss, graphs)):
+        pi = pc.params(k=8, R=32, L_search=96, L_dep=96, n_clusters=comps[i], hash_slots=p.hash_slots,
+                       block_warps=p.block_warps)
+        ws = pc.workspace(ds, pi)
+        singles.append((ds, G, pi, ws))
+
+    def seq():
+        for ds, G, pi, ws in singles:
+            d = pc.pecann_density(ds, G, pi, ws=ws)
+            dp = pc.pecann_dependent_points(ds, G, pi, d["rank_key"], d["knn_ids"], d["knn_dist"], ws=ws)
+            pc.pecann_cluster(d["density"], dp["dep"], dp["dep_dist"], pi, count=False)
+
+    t_seq = _timed_steps(seq, 1, max(1, args.steps // 4))
+    # recall on 32 sampled points per set
+    got = batch.out["knn_dist"].cpu().numpy()
+    rec = []
+    for i, (X, _, _) in enumerate(sets):
+        qs = synth.sample_ids(len(X), 32, seed=i)
+        _, ex = exact.exact_knn_queries(X, qs, 8)
+        rec.append(exact.knn_recall(got[batch.offsets[i] + qs], ex))
+    N = batch.N
+    out = {"metric": METRIC, "value": N / t_graph, "unit": UNIT, "workload": "batched64",
+           "config": {"workload": "64 FP32 Gaussian mixtures, n log-uniform [2000, 200000], d in {96,128,256,384}, "
+                                  "5-500 components; R=32 L=96 k=8; build 2 passes L=192", "points": N},
+           "ms_per_step_graph": t_graph * 1e3, "ms_per_step_batched_no_graph": t_plain * 1e3,
+           "ms_per_step_sets_one_by_one": t_seq * 1e3, "points_per_s_one_by_one": N / t_seq,
+           "autotune": {k2: v for k2, v in tune.items() if k2 != "tried"}, "autotune_tried": tune.get("tried"),
+           "recall": float(np.mean(rec)), "build_s": build_s}
+    print(json.dumps(out), flush=True)
+
+
+def run_reduced(args, kind):
+    """FP32 traversal vs BF16 traversal (exact FP32 re-rank) on the same graph."""
+    import torch
+
+    from oracle import exact
+    from paper_2312_03940_gb300 import pecann as pc
+    from paper_2312_03940_gb300 import synth
+
+    pc.load_library()
+    if kind == "sphere384":
+        n = args.n if args.n != WORKLOAD["n"] else 1_000_000
+        X, gt = synth.powerlaw_sphere(n=n)
+        metric, R, L, k, alpha, ncl = pc.L2, 48, 128, 20, 1.1, 10_000
+        dens_fns = [("kth", pc.DENS_KTH), ("exp-sum", pc.DENS_EXPSUM)]
+        desc = f"unit-norm power-law-spectrum sphere n={n} d=384, 10,000 Pareto(1.5) clusters; R=48 L=128 alpha=1.1 k=20"
+    else:
+        n = args.n if args.n != WORKLOAD["n"] else 1_280_000
+        X, gt = synth.vmf_like(n=n)
+        metric, R, L, k, alpha, ncl = pc.IP, 64, 200, 16, 1.2, 1000
+        dens_fns = [("kth", pc.DENS_KTH)]
+        desc = f"unit-norm vMF-like n={n} d=1024 inner product, 1,000 clusters; R=64 L=200 k=16"
+    Xd = torch.from_numpy(X).cuda()
+    del X
+    Xb = Xd.to(torch.bfloat16).contiguous()
+    ds32 = pc.Dataset(Xd, metric=metric)
+    dsb = pc.Dataset(Xb, metric=metric, data_f32=Xd)
+    p = pc.params(k=k, R=R, L_build=2 * L, L_search=L, L_dep=L, alpha=alpha, build_passes=2,
+                  n_start=max(16, min(n, 8192 * n // 1_000_000)), n_clusters=ncl)
+    t0 = time.perf_counter()
+    G, _ = pc.pecann_build_graph(ds32, p, order=torch.from_numpy(synth.insertion_order(n)).cuda())
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Xh = Xd.cpu().numpy()
+    qs = synth.sample_ids(n, 1000)
+    _, ex = exact.exact_knn_queries(Xh, qs, k, metric=metric)
+    res = {}
+    for name, fn in dens_fns:
+        p.density = fn
+        for tag, ds in (("fp32", ds32), ("bf16", dsb)):
+            ws = pc.workspace(ds, p)
+            out = {}
+
+            def step():
+                d = pc.pecann_density(ds, G, p, ws=ws)
+                dp = pc.pecann_dependent_points(ds, G, p, d["rank_key"], d["knn_ids"], d["knn_dist"], ws=ws)
+                lab, _ = pc.pecann_cluster(d["density"], dp["dep"], dp["dep_dist"], p, count=False)
+                out.update(d, labels=lab)
+
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t = _timed_steps(step, args.warmup, args.steps)
+            e0.record()
+            pc.pecann_density(ds, G, p, ws=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            res[f"{name}/{tag}"] = {"points_per_s": n / t, "ms_per_step": t * 1e3,
+                                    "density_ms": e0.elapsed_time(e1),
+                                    "recall": exact.knn_recall(out["knn_dist"][torch.from_numpy(qs).cuda()].cpu().numpy(),
+                                                               ex),
+                                    "labels": out["labels"].cpu().numpy()}
+        res[f"{name}/bf16"]["ari_vs_fp32"] = exact.ari(res[f"{name}/bf16"]["labels"], res[f"{name}/fp32"]["labels"])
+    for v in res.values():
+        v.pop("labels")
+    print(json.dumps({"workload": kind, "config": {"workload": desc, "build_s": build_s}, "results": res}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched64":
+        run_batched64(args)
+    elif args.workload in ("sphere384", "vmf1024"):
+        run_reduced(args, args.workload)
     else:
         run_ours(args)
 

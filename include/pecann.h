@@ -121,6 +121,9 @@ typedef struct {
                                 then a second over all points with alpha   build              */
   int32_t rerank_k;          /* BF16 traversal: candidates per point re-scored in FP32
                                 (0: min(L_search, 4k); must be >= k)         density          */
+  int32_t block_warps;       /* warps per block of the search kernel (1, 2, 4 or 8; 0 =
+                                automatic). Like hash_slots it changes speed, never results */
+  int32_t reserved2;
   uint64_t seed;             /* insertion order when none is given         build              */
 } pecann_params;
 
@@ -141,7 +144,7 @@ typedef struct {
    alpha 1.1, n_start 16, batch_frac 0.02, visit_cap 0, dep_threshold 300,
    max_dep_rounds 30, max_dep_beam 8192, kth density, no normalisation,
    product center, rho_min 0, delta_min 0, n_clusters 1, hash_slots 0,
-   collect_work 0, build_passes 1, rerank_k 0, seed 0. */
+   collect_work 0, build_passes 1, rerank_k 0, block_warps 0, seed 0. */
 PECANN_API void pecann_params_default(pecann_params* p);
 
 /* Static string for a status code. */

@@ -205,6 +205,7 @@ void pecann_params_default(pecann_params* p) {
   p->collect_work = 0;
   p->build_passes = 1;
   p->rerank_k = 0;
+  p->block_warps = 0;
   p->seed = 0;
 }
 
@@ -279,6 +280,7 @@ pecann_status pecann_search(const pecann_dataset* ds, const int32_t* d_graph, in
   a.stage = (std::max(R, 64) + 31) & ~31;
   a.mode = MODE_RAW;
   a.metric = dv.metric;
+  a.block_warps = p->block_warps;
   a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
   a.k = k;
   a.out_ids = d_ids;
@@ -354,6 +356,7 @@ pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, c
   a.stage = (p->R + 31) & ~31;
   a.mode = MODE_KNN;
   a.metric = dv.metric;
+  a.block_warps = p->block_warps;
   a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
   a.k = p->k;
   a.out_ids = d_knn_ids;
@@ -455,7 +458,8 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
     a.stage = (p->R + 31) & ~31;
     a.mode = MODE_DEP;
     a.metric = dv.metric;
-    a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
+    a.block_warps = p->block_warps;
+  a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
     a.rank_key = d_rank_key;
     a.lam = d_dep;
     a.delta = d_dep_dist;

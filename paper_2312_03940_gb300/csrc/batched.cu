@@ -567,6 +567,7 @@ extern "C" pecann_status pecann_run_batched(int32_t n_sets, const pecann_dataset
   a.stage = (std::max(p->R, 64) + 31) & ~31;
   a.mode = MODE_KNN;
   a.metric = hp.metric;
+  a.block_warps = p->block_warps;
   a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
   a.k = p->k;
   a.out_ids = d_knn_ids;

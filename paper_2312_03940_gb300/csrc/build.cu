@@ -498,6 +498,7 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
   a.vcap = vcap;
   a.mode = MODE_BUILD;
   a.metric = dv.metric;
+  a.block_warps = p.block_warps;
   a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, a.vcap, true);
   a.vis_ids = vis_ids;
   a.vis_dis = vis_dis;

@@ -43,6 +43,7 @@ struct SearchArgs {
   int mode;
   int metric;
   int warp_bytes;     // shared memory per warp
+  int block_warps;    // warps per block (0 = automatic)
   // RAW / KNN outputs
   int k;
   int32_t* out_ids;

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 4 : 5) k_search(SearchArgs a) {
 template <int DT, int METRIC, int W, int CPL, bool BATCHED>
 inline cudaError_t launch_inst(const SearchArgs& a, cudaStream_t st) {
   auto kern = k_search<DT, METRIC, W, CPL, BATCHED>;
-  int wpb = 8;
+  int wpb = (a.block_warps >= 1 && a.block_warps <= 8) ? a.block_warps : 8;
   while (wpb > 1 && (size_t)wpb * a.warp_bytes > 200 * 1024) wpb >>= 1;
   size_t smem = (size_t)wpb * a.warp_bytes;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;

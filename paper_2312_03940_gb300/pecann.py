@@ -34,7 +34,8 @@ class PecannParams(ctypes.Structure):
                 ("max_dep_beam", ctypes.c_int32), ("density", ctypes.c_int32),
                 ("normalize_density", ctypes.c_int32), ("center", ctypes.c_int32), ("rho_min", ctypes.c_float),
                 ("delta_min", ctypes.c_float), ("n_clusters", ctypes.c_int32), ("hash_slots", ctypes.c_int32),
-                ("collect_work", ctypes.c_int32), ("build_passes", ctypes.c_int32), ("rerank_k", ctypes.c_int32),
+                ("collect_work", ctypes.c_int32), ("build_passes", ctypes.c_int32), ("rerank_k", ctypes.c_int32), ("block_warps", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 

@@ -129,14 +129,15 @@ def batched_sets(count: int = 64, n_lo: int = 2_000, n_hi: int = 200_000, dims=(
                  comp_lo: int = 5, comp_hi: int = 500, seed: int = SEED_BASE + 4):
     """`count` independent Gaussian mixtures: n log-uniform in [n_lo, n_hi],
     d uniform over `dims`, components uniform in [comp_lo, comp_hi].
-    Returns a list of (X float32, labels)."""
+    Returns a list of (X float32, labels, components)."""
     g = rng(seed)
     out = []
     for _ in range(count):
         n = int(round(np.exp(g.uniform(np.log(n_lo), np.log(n_hi)))))
         d = int(g.choice(dims))
         comp = int(g.integers(comp_lo, comp_hi + 1))
-        out.append(gaussian_mixture(n, d, comp, sigma=1.0, box=10.0, seed=int(g.integers(1 << 31))))
+        X, lab = gaussian_mixture(n, d, comp, sigma=1.0, box=10.0, seed=int(g.integers(1 << 31)))
+        out.append((X, lab, comp))
     return out
 
 

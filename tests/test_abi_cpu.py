@@ -44,8 +44,8 @@ def test_params_default_and_strings(lib):
 
 
 def test_struct_layout_matches_header(lib):
-    # pecann_params: 22 four-byte fields, then a uint64 -> 96 bytes
-    assert ctypes.sizeof(pc.PecannParams) == 96
+    # pecann_params: 24 four-byte fields, then a uint64 -> 104 bytes
+    assert ctypes.sizeof(pc.PecannParams) == 104
     assert ctypes.sizeof(pc.PecannDataset) == 48
 
 
