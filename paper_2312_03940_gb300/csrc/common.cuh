@@ -228,6 +228,60 @@ __device__ __forceinline__ float group_dis(const uint4 (&q)[CPL], const uint4 (&
   return 1.0f - (float)s;
 }
 
+// ----------------------------------------------------------------- paired FP32 rows
+// Blackwell's packed f32x2 instructions round each half exactly like the
+// scalar instruction, so scoring two candidate rows with one packed register
+// pair (low half: first row, high half: second row) keeps each row's
+// canonical sequence of operations and gives the same bits, with half the
+// arithmetic instructions.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+  return f;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Canonical partial sums of one lane for two FP32 rows at once.
+template <int METRIC, int CPL>
+__device__ __forceinline__ float2 partial_f32_pair(const uint4 (&q)[CPL], const uint4 (&r0)[CPL],
+                                                   const uint4 (&r1)[CPL]) {
+  unsigned long long acc = pk2(0.0f, 0.0f);
+#pragma unroll
+  for (int t = 0; t < CPL; t++) {
+    const unsigned qa[4] = {q[t].x, q[t].y, q[t].z, q[t].w};
+    const unsigned a0[4] = {r0[t].x, r0[t].y, r0[t].z, r0[t].w};
+    const unsigned a1[4] = {r1[t].x, r1[t].y, r1[t].z, r1[t].w};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const float qf = __uint_as_float(qa[e]);
+      const unsigned long long qq = pk2(qf, qf);
+      const unsigned long long rr = pk2(__uint_as_float(a0[e]), __uint_as_float(a1[e]));
+      if (METRIC == MET_L2) {
+        const unsigned long long d = sub2(qq, rr);
+        acc = fma2(d, d, acc);
+      } else {
+        acc = fma2(qq, rr, acc);
+      }
+    }
+  }
+  return upk2(acc);
+}
+
 // ----------------------------------------------------------------- warp helpers
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -130,11 +130,31 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
         for (int t = 0; t < CPL; t++) r[u][t] = make_uint4(0, 0, 0, 0);
       }
     }
+    if constexpr (DT == DT_F32 && UNR % 2 == 0) {
+      // two rows per packed instruction (same bits as one row at a time)
 #pragma unroll
-    for (int u = 0; u < UNR; u++) {
-      float dv = group_dis<DT, METRIC, W, CPL>(qv, r[u]);
-      int c = c0 + u * GR + g;
-      if (gl == 0 && c < nc) w.ckeys[c] = make_key(dv, w.cids[c]);
+      for (int u = 0; u < UNR; u += 2) {
+        float2 s = partial_f32_pair<METRIC, CPL>(qv, r[u], r[u + 1]);
+#pragma unroll
+        for (int off = W / 2; off >= 1; off >>= 1) {
+          s.x += __shfl_xor_sync(FULL, s.x, off);
+          s.y += __shfl_xor_sync(FULL, s.y, off);
+        }
+        if (METRIC == MET_IP) {
+          s.x = 1.0f - s.x;
+          s.y = 1.0f - s.y;
+        }
+        const int c = c0 + u * GR + g, c1 = c + GR;
+        if (gl == 0 && c < nc) w.ckeys[c] = make_key(s.x, w.cids[c]);
+        if (gl == 0 && c1 < nc) w.ckeys[c1] = make_key(s.y, w.cids[c1]);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < UNR; u++) {
+        float dv = group_dis<DT, METRIC, W, CPL>(qv, r[u]);
+        int c = c0 + u * GR + g;
+        if (gl == 0 && c < nc) w.ckeys[c] = make_key(dv, w.cids[c]);
+      }
     }
   }
   __syncwarp();
