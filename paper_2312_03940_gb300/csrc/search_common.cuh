@@ -173,6 +173,8 @@ __device__ __forceinline__ int count_below(const uint64_t* s, int m, uint64_t x)
   return lo;
 }
 
+__device__ __forceinline__ int merge_filtered(WarpSmem& w, int& nb, int Lw, int m, int& cursor, int lane);
+
 // Merge the staged candidate keys into the beam (keep the Lw smallest keys,
 // no duplicates). Returns the number of keys merged. Collective.
 __device__ __forceinline__ int merge_cands(WarpSmem& w, int& nb, int Lw, int nc, int& cursor, int lane) {
@@ -189,7 +191,43 @@ __device__ __forceinline__ int merge_cands(WarpSmem& w, int& nb, int Lw, int nc,
     m += __popc(bm);
     __syncwarp();
   }
+  return merge_filtered(w, nb, Lw, m, cursor, lane);
+}
+
+// Merge the m candidate keys at the front of ckeys (all better than the
+// beam's current Lw-th entry, or the beam is not full) into the beam.
+__device__ __forceinline__ int merge_filtered(WarpSmem& w, int& nb, int Lw, int m, int& cursor, int lane) {
   if (m == 0) return 0;
+  if (m <= 3) {
+    // a few survivors (the usual case once the beam is full): insert them one
+    // at a time -- rank by one ballot per 32 entries, shift the tail by one
+    for (int i = 0; i < m; i++) {
+      const uint64_t x = w.ckeys[i];
+      int pos = 0;
+      bool dup = false;
+      for (int b = 0; b < nb; b += 32) {
+        const int j = b + lane;
+        const uint64_t e = j < nb ? key_clean(w.beam[j]) : KEY_NONE;
+        pos += __popc(__ballot_sync(FULL, e < x));
+        dup |= e == x;
+      }
+      if (__any_sync(FULL, dup) || pos >= Lw) continue;
+      const int top = min(nb, Lw - 1);  // entries [pos, top) move up by one
+      for (int hi = top - 1; hi >= pos; hi -= 32) {
+        const int idx = hi - lane;
+        uint64_t e = 0;
+        if (idx >= pos) e = w.beam[idx];
+        __syncwarp();
+        if (idx >= pos) w.beam[idx + 1] = e;
+        __syncwarp();
+      }
+      if (lane == 0) w.beam[pos] = x;
+      __syncwarp();
+      nb = min(nb + 1, Lw);
+      if (pos < cursor) cursor = pos;
+    }
+    return m;
+  }
   // 2) duplicates: of an earlier survivor, or of a beam entry
   for (int i = lane; i < m; i += 32) {
     uint64_t kk = w.ckeys[i];
