@@ -121,6 +121,23 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- helpers
 
+def max_over_ranks(elapsed_s: float, dist=None, device=None) -> float:
+    """The slowest rank's timed region (every rank gets it)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return elapsed_s
+    import torch
+
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(points_per_rank: int, steps: int, world: int, elapsed_s: float) -> float:
+    """Whole-job points/s of `world` replicas that each processed
+    points_per_rank points `steps` times within the slowest rank's time."""
+    return world * points_per_rank * steps / elapsed_s
+
+
 def source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2312_03940_gb300", "csrc")
@@ -299,13 +316,9 @@ def run_ours(args):
     barrier()
     launches = pc.pecann_kernel_launches() - l0
     clk = clocks.stop()
-    elapsed = t0.elapsed_time(t1) / 1000.0
-    if dist:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1000.0, dist, dev)
     dens_avg_s = float(np.mean([a.elapsed_time(b) for a, b in timed_density])) / 1000.0
-    value = world * n * args.steps / elapsed
+    value = replica_throughput(n, args.steps, world, elapsed)
     stats = pc.pecann_dependent_points(ds, G, p, dens_out["rank_key"], dens_out["knn_ids"], dens_out["knn_dist"],
                                        ws=ws, out=dep_out)["stats"]
     torch.cuda.synchronize()
