@@ -52,6 +52,11 @@ __device__ __forceinline__ float ord2f(uint32_t u) {
 __device__ __forceinline__ uint64_t make_key(float dis, int32_t id) {
   return ((uint64_t)f2ord(dis) << 32) | (uint32_t)id;
 }
+// Same key for a dissimilarity known to be >= +0 (squared L2): the sign
+// branch of f2ord is not needed.
+__device__ __forceinline__ uint64_t make_key_nonneg(float dis, int32_t id) {
+  return ((uint64_t)(__float_as_uint(dis) | 0x80000000u) << 32) | (uint32_t)id;
+}
 __device__ __forceinline__ uint64_t key_clean(uint64_t k) { return k & ~VFLAG; }
 __device__ __forceinline__ int32_t key_id(uint64_t k) { return (int32_t)(k & 0x7fffffffu); }
 __device__ __forceinline__ float key_dis(uint64_t k) { return ord2f((uint32_t)(k >> 32)); }

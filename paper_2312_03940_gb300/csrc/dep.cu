@@ -68,44 +68,74 @@ __global__ void k_compact_unfinished(const int32_t* src, int64_t m, const int32_
 }
 
 // Exact tail: lambda_i <- DPBruteForce(x_i, P) for the listed points. Block b
-// scans points [b*chunk, (b+1)*chunk); each warp takes listed queries in turn
-// and keeps the smallest (dis, id) key among points ranked above the query;
-// one atomicMin per (warp, query) combines the chunks.
+// scans points [b*chunk, (b+1)*chunk) against the listed queries, TAIL_QT at
+// a time: the query rows are staged in shared memory, each group of W lanes
+// holds one point row in registers and scores it against every staged query,
+// so a point row is read once per TAIL_QT queries. The smallest (dis, id) key
+// among points ranked above each query is kept in shared memory and merged
+// into best[u] with one atomicMin per (block, query).
+static const int DEP_TAIL_QT = 32;
+
 template <int DT, int METRIC, int W, int CPL>
 __global__ void __launch_bounds__(256) k_dep_bf(const uint8_t* X, int64_t row_bytes, int64_t n, int C,
                                                  const int32_t* list, int64_t m, const float* rk,
                                                  int64_t chunk, unsigned long long* best) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ unsigned long long tile_best[DEP_TAIL_QT];
+  __shared__ int32_t tile_q[DEP_TAIL_QT];
+  __shared__ float tile_rk[DEP_TAIL_QT];
   constexpr int GR = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int g = lane / W, gl = lane % W;
   const int64_t j0 = (int64_t)blockIdx.x * chunk;
   const int64_t j1 = min(n, j0 + chunk);
-  for (int64_t u = wib; u < m; u += nw) {
-    const int32_t q = list[u];
-    uint4 qv[CPL];
-    load_row<W, CPL, false>(X + (int64_t)q * row_bytes, gl, C, qv);
-    unsigned long long mine = KEY_NONE;
-    for (int64_t jb = j0; jb < j1; jb += GR) {
-      int64_t j = jb + g;
+  uint4* qrows = reinterpret_cast<uint4*>(smem);  // DEP_TAIL_QT rows of C chunks
+  for (int64_t ub = 0; ub < m; ub += DEP_TAIL_QT) {
+    const int nq = (int)(m - ub < DEP_TAIL_QT ? m - ub : DEP_TAIL_QT);
+    for (int i = threadIdx.x; i < nq * C; i += blockDim.x) {
+      const int qq = i / C, c = i % C;
+      qrows[qq * C + c] = __ldg(reinterpret_cast<const uint4*>(X + (int64_t)list[ub + qq] * row_bytes) + c);
+    }
+    if (threadIdx.x < DEP_TAIL_QT) {
+      tile_best[threadIdx.x] = KEY_NONE;
+      if (threadIdx.x < nq) {
+        const int32_t q = list[ub + threadIdx.x];
+        tile_q[threadIdx.x] = q;
+        tile_rk[threadIdx.x] = __ldg(rk + q);
+      }
+    }
+    __syncthreads();
+    for (int64_t jb = j0 + (int64_t)wib * GR; jb < j1; jb += (int64_t)nw * GR) {
+      const int64_t j = jb + g;
       uint4 r[CPL];
+      float rkj = 0.0f;
       if (j < j1) {
         load_row<W, CPL, false>(X + j * row_bytes, gl, C, r);
+        rkj = __ldg(rk + j);
       } else {
 #pragma unroll
         for (int t = 0; t < CPL; t++) r[t] = make_uint4(0, 0, 0, 0);
       }
-      float dv = group_dis<DT, METRIC, W, CPL>(qv, r);
-      if (gl == 0 && j < j1 && j != q && ranks_above(rk, (int32_t)j, q)) {
-        unsigned long long kk = make_key(dv, (int32_t)j);
-        mine = kk < mine ? kk : mine;
+      for (int qq = 0; qq < nq; qq++) {
+        uint4 qv[CPL];
+#pragma unroll
+        for (int t = 0; t < CPL; t++) {
+          const int ch = gl + W * t;
+          qv[t] = ch < C ? qrows[qq * C + ch] : make_uint4(0, 0, 0, 0);
+        }
+        const float dv = group_dis<DT, METRIC, W, CPL>(qv, r);
+        const int32_t q = tile_q[qq];
+        const float rkq = tile_rk[qq];
+        // j ranks above q: larger key, or equal key and smaller id
+        if (gl == 0 && j < j1 && j != q && (rkj > rkq || (rkj == rkq && j < q))) {
+          const unsigned long long kk = make_key(dv, (int32_t)j);
+          if (kk < tile_best[qq]) atomicMin(tile_best + qq, kk);
+        }
       }
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      unsigned long long o = __shfl_xor_sync(FULL, mine, off);
-      mine = o < mine ? o : mine;
-    }
-    if (lane == 0 && mine != KEY_NONE) atomicMin(best + u, mine);
+    __syncthreads();
+    if (threadIdx.x < nq && tile_best[threadIdx.x] != KEY_NONE) atomicMin(best + ub + threadIdx.x, tile_best[threadIdx.x]);
+    __syncthreads();
   }
 }
 
@@ -135,8 +165,12 @@ static cudaError_t launch_dep_bf_inst(const DataView& dv, const int32_t* list, i
   int64_t chunk = (dv.n + blocks_target - 1) / blocks_target;
   if (chunk < 256) chunk = 256;
   int64_t grid = (dv.n + chunk - 1) / chunk;
-  k_dep_bf<DT, METRIC, W, CPL><<<(unsigned)grid, 256, 0, st>>>(dv.X, dv.row_bytes, dv.n, dv.C, list, m, rk,
-                                                               chunk, best); note_launch();
+  const size_t smem = (size_t)DEP_TAIL_QT * dv.C * 16;
+  auto kern = k_dep_bf<DT, METRIC, W, CPL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, 256, smem, st>>>(dv.X, dv.row_bytes, dv.n, dv.C, list, m, rk, chunk, best);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -153,7 +153,8 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
       for (int u = 0; u < UNR; u++) {
         float dv = group_dis<DT, METRIC, W, CPL>(qv, r[u]);
         int c = c0 + u * GR + g;
-        if (gl == 0 && c < nc) w.ckeys[c] = make_key(dv, w.cids[c]);
+        if (gl == 0 && c < nc)
+          w.ckeys[c] = METRIC == MET_L2 ? make_key_nonneg(dv, w.cids[c]) : make_key(dv, w.cids[c]);
       }
     }
   }
