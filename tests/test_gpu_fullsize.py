@@ -1,0 +1,104 @@
+"""Full-size checks: the benchmark's 1,000,000 x 128 uint8 workload and its
+launch configuration (R=64, L=128, k=10, one query per warp over all points).
+
+The oracle cannot process a million points in a test, so outputs are checked
+on samples it computes one by one, and through properties that hold at any
+size. Inputs never come from the CUDA path: the parity part runs on a seeded
+random out-degree-64 graph drawn here, not on a GPU-built graph.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import exact
+from paper_2312_03940_gb300 import pecann as pc
+from paper_2312_03940_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+N, D, R, L, K = 1_000_000, 128, 64, 128, 10
+
+
+@pytest.fixture(scope="module")
+def data():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    pc.load_library()
+    X, gt = synth.u8_mixture(n=N, d=D)
+    return X, gt
+
+
+def test_fullsize_search_density_and_dependents_against_the_oracle(data):
+    X, _ = data
+    g = np.random.default_rng(2026)
+    G = g.integers(0, N, size=(N, R), dtype=np.int64).astype(np.int32)  # duplicates and self ids included
+    p = pc.params(k=K, R=R, L_search=L, L_dep=L, n_clusters=100)
+    ds = pc.Dataset(torch.from_numpy(X).cuda())
+    Gd = torch.from_numpy(G).cuda()
+    ws = pc.workspace(ds, p)
+    dens = pc.pecann_density(ds, Gd, p, ws=ws)
+    dep = pc.pecann_dependent_points(ds, Gd, p, dens["rank_key"], dens["knn_ids"], dens["knn_dist"], ws=ws)
+    ids = dens["knn_ids"].cpu().numpy()
+    dist = dens["knn_dist"].cpu().numpy()
+    key = dens["rank_key"].cpu().numpy()
+    lam = dep["dep"].cpu().numpy()
+    delta = dep["dep_dist"].cpu().numpy()
+    P = oracle.Points(X)
+    # 1) Algorithm 1 for sampled queries, bit for bit
+    qs = synth.sample_ids(N, 120, seed=7)
+    for q in qs:
+        oi, od = oracle.greedy_search(P, G, int(q), [int(q)], L=L, k=K)
+        assert len(oi) == K
+        assert (ids[q] == oi).all(), q
+        assert (dist[q] == oracle.out_dist(P, od)).all(), q
+    # 2) round 0 for sampled points, recomputed by the oracle: its own k-NN of
+    #    the point and the densities of those neighbours from their own searches
+    def kth_density(i):
+        _, d_ = oracle.greedy_search(P, G, int(i), [int(i)], L=L, k=K)
+        return np.float32(1.0) / np.float32(oracle.out_dist(P, d_)[-1])
+
+    for i in synth.sample_ids(N, 30, seed=8):
+        oi, _ = oracle.greedy_search(P, G, int(i), [int(i)], L=L, k=K)
+        ki = kth_density(i)
+        assert key[i] == ki
+        first = -1
+        for j in oi:
+            kj = kth_density(j)
+            if kj > ki or (kj == ki and j < i):
+                first = int(j)
+                break
+        if first >= 0:
+            assert lam[i] == first, i
+    # 3) properties at full size: every dependent point ranks strictly above
+    #    its point, exactly one point (the maximum) has none, delta is the
+    #    oracle's distance of the pair
+    has = lam >= 0
+    assert (~has).sum() == 1
+    top = int(np.flatnonzero(~has)[0])
+    order = exact.rank_order(key.astype(np.float64))
+    assert order[0] == top
+    rank = np.empty(N, np.int64)
+    rank[order] = np.arange(N)
+    assert (rank[lam[has]] < rank[np.flatnonzero(has)]).all()
+    for i in synth.sample_ids(N, 200, seed=9):
+        if lam[i] >= 0:
+            assert delta[i] == np.float32(oracle.out_dist(P, oracle.dis(P, int(i), int(lam[i]))))
+
+
+def test_fullsize_build_invariants_and_recall(data):
+    X, _ = data
+    p = pc.params(k=K, R=R, L_build=256, L_search=L, alpha=1.2, n_start=8192, build_passes=2)
+    ds = pc.Dataset(torch.from_numpy(X).cuda())
+    G, deg = pc.pecann_build_graph(ds, p, order=torch.from_numpy(synth.insertion_order(N)).cuda())
+    Gh = G.cpu().numpy()
+    degh = deg.cpu().numpy()
+    assert ((Gh >= 0).sum(1) == degh).all() and degh.max() <= R
+    rows = np.arange(N)[:, None]
+    valid = Gh >= 0
+    assert not (valid & (Gh == rows)).any()  # no self loops
+    srt = np.sort(np.where(valid, Gh, -1 - np.arange(R)[None, :]), axis=1)
+    assert not (np.diff(srt, axis=1) == 0).any()  # no duplicate edges
+    dens = pc.pecann_density(ds, G, p)
+    qs = synth.sample_ids(N, 300, seed=10)
+    _, ex = exact.exact_knn_queries(X, qs, K)
+    assert exact.knn_recall(dens["knn_dist"][torch.from_numpy(qs).cuda()].cpu().numpy(), ex) >= 0.95
