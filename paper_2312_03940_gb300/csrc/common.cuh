@@ -308,6 +308,12 @@ __device__ __forceinline__ int lower_bound_key(const uint64_t* a, int n, uint64_
   return lo;
 }
 
+// Offset id * stride for a non-negative id and a stride below 2^32 (a row is
+// at most 4 KB, an out-list at most R ids): one 32 x 32 -> 64-bit multiply.
+__device__ __forceinline__ uint64_t wide_mul(int32_t id, int64_t stride) {
+  return (uint64_t)(uint32_t)id * (uint32_t)stride;
+}
+
 __device__ __forceinline__ uint32_t hash_slot(int32_t id, int log2h) {
   return ((uint32_t)id * 0x9E3779B1u) >> (32 - log2h);
 }

@@ -74,7 +74,7 @@ __device__ __forceinline__ int admit(const SearchArgs& a, WarpSmem& w, int32_t y
 // Candidate ids from the out-list of p.
 __device__ __forceinline__ int gather_out(const SearchArgs& a, WarpSmem& w, int32_t p, int32_t q,
                                           int lane) {
-  const int32_t* row = a.G + (int64_t)p * a.R;
+  const int32_t* row = a.G + wide_mul(p, a.R);
   int nc = 0;
   for (int b = 0; b < a.R; b += 32) {
     int idx = b + lane;
@@ -114,7 +114,7 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
     // rows beyond the first batch: start their fetch now, so the later
     // batches find them in L2 instead of waiting a full DRAM round trip each
     for (int c = GR * UNR + lane; c < nc; c += 32) {
-      const uint8_t* r = a.X + (int64_t)w.cids[c] * a.row_bytes;
+      const uint8_t* r = a.X + wide_mul(w.cids[c], a.row_bytes);
       for (int64_t off = 0; off < a.row_bytes; off += 128) prefetch_l2(r + off);
     }
   }
@@ -124,7 +124,7 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
     for (int u = 0; u < UNR; u++) {
       int c = c0 + u * GR + g;
       if (c < nc) {
-        load_row<W, CPL, true>(a.X + (int64_t)w.cids[c] * a.row_bytes, gl, a.C, r[u]);
+        load_row<W, CPL, true>(a.X + wide_mul(w.cids[c], a.row_bytes), gl, a.C, r[u]);
       } else {
 #pragma unroll
         for (int t = 0; t < CPL; t++) r[u][t] = make_uint4(0, 0, 0, 0);
@@ -174,6 +174,35 @@ __device__ __forceinline__ int count_below(const uint64_t* s, int m, uint64_t x)
   return lo;
 }
 
+// Rank of key x in the sorted beam (number of entries below it) and whether
+// x is already there. Up to 1024 entries: one ballot over every s-th entry
+// (s = ceil(nb / 32)) finds the stride that brackets x, a second ballot ranks
+// it inside that stride. Collective; the result is the same on every lane.
+__device__ __forceinline__ int beam_rank(const uint64_t* beam, int nb, uint64_t x, int lane, bool* dup) {
+  int pos = 0;
+  if (nb <= 1024) {
+    const int s = (nb + 31) >> 5;
+    const int j = lane * s;
+    const uint64_t e = j < nb ? key_clean(beam[j]) : KEY_NONE;
+    const int c1 = __popc(__ballot_sync(FULL, e < x));
+    if (c1 > 0) {
+      // beam[(c1 - 1) s] < x, and beam[c1 s] >= x when it exists
+      const int base = (c1 - 1) * s + 1, lim = min(nb, c1 * s);
+      const int t = base + lane;
+      const uint64_t e2 = t < lim ? key_clean(beam[t]) : KEY_NONE;
+      pos = base + __popc(__ballot_sync(FULL, e2 < x));
+    }
+  } else {
+    for (int b = 0; b < nb; b += 32) {
+      const int j = b + lane;
+      const uint64_t e = j < nb ? key_clean(beam[j]) : KEY_NONE;
+      pos += __popc(__ballot_sync(FULL, e < x));
+    }
+  }
+  *dup = pos < nb && key_clean(beam[pos]) == x;
+  return pos;
+}
+
 __device__ __forceinline__ int merge_filtered(WarpSmem& w, int& nb, int Lw, int m, int& cursor, int lane);
 
 // Merge the staged candidate keys into the beam (keep the Lw smallest keys,
@@ -201,18 +230,12 @@ __device__ __forceinline__ int merge_filtered(WarpSmem& w, int& nb, int Lw, int 
   if (m == 0) return 0;
   if (m <= 3) {
     // a few survivors (the usual case once the beam is full): insert them one
-    // at a time -- rank by one ballot per 32 entries, shift the tail by one
+    // at a time -- rank in the beam, shift the tail by one
     for (int i = 0; i < m; i++) {
       const uint64_t x = w.ckeys[i];
-      int pos = 0;
-      bool dup = false;
-      for (int b = 0; b < nb; b += 32) {
-        const int j = b + lane;
-        const uint64_t e = j < nb ? key_clean(w.beam[j]) : KEY_NONE;
-        pos += __popc(__ballot_sync(FULL, e < x));
-        dup |= e == x;
-      }
-      if (__any_sync(FULL, dup) || pos >= Lw) continue;
+      bool dup;
+      const int pos = beam_rank(w.beam, nb, x, lane, &dup);
+      if (dup || pos >= Lw) continue;
       const int top = min(nb, Lw - 1);  // entries [pos, top) move up by one
       for (int hi = top - 1; hi >= pos; hi -= 32) {
         const int idx = hi - lane;

@@ -19,7 +19,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
     return;
   }
   uint4 qv[CPL];
-  load_row<W, CPL, false>(a.X + (int64_t)q * a.row_bytes, gl, a.C, qv);
+  load_row<W, CPL, false>(a.X + wide_mul(q, a.row_bytes), gl, a.C, qv);
   for (int i = lane; i < H; i += 32) w.hash[i] = -1;
   __syncwarp();
   if (lane == 0) {
@@ -66,7 +66,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
     uint64_t e = w.beam[pos];
     // the runner-up is usually the next point popped: fetch its out-list early
     if (next >= 0 && lane < (a.R * 4 + 127) / 128)
-      prefetch_l2(a.G + (int64_t)key_id(w.beam[next]) * a.R + lane * 32);
+      prefetch_l2(a.G + wide_mul(key_id(w.beam[next]), a.R) + lane * 32);
     __syncwarp();
     if (lane == 0) w.beam[pos] = e | VFLAG;  // V <- V u {p*}
     __syncwarp();
