@@ -123,7 +123,10 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
       int c = c0 + u * GR + g;
-      if (c < nc) {
+      if constexpr (DT == DT_U8) {
+        // a slot past the last candidate rescores the last one (discarded)
+        load_row<W, CPL, true>(a.X + wide_mul(w.cids[min(c, nc - 1)], a.row_bytes), gl, a.C, r[u]);
+      } else if (c < nc) {
         load_row<W, CPL, true>(a.X + wide_mul(w.cids[c], a.row_bytes), gl, a.C, r[u]);
       } else {
 #pragma unroll
@@ -148,6 +151,24 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
         if (gl == 0 && c < nc) w.ckeys[c] = make_key(s.x, w.cids[c]);
         if (gl == 0 && c1 < nc) w.ckeys[c1] = make_key(s.y, w.cids[c1]);
       }
+    } else if constexpr (DT == DT_U8 && UNR == 4) {
+      // integer partials, exact in any order: reduce the group's four rows
+      // together. The first two steps halve the rows a lane carries (it keeps
+      // row u = 2*[gl & W/2] + [gl & W/4]), plain butterfly steps finish it.
+      unsigned pt[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) pt[u] = Partial<DT_U8, MET_L2, CPL>::run(qv, r[u]);
+      const bool b2 = (gl & (W / 2)) != 0, b1 = (gl & (W / 4)) != 0;
+      unsigned k0 = b2 ? pt[2] : pt[0], k1 = b2 ? pt[3] : pt[1];
+      const unsigned s0 = b2 ? pt[0] : pt[2], s1 = b2 ? pt[1] : pt[3];
+      k0 += __shfl_xor_sync(FULL, s0, W / 2);
+      k1 += __shfl_xor_sync(FULL, s1, W / 2);
+      unsigned k = b1 ? k1 : k0;
+      k += __shfl_xor_sync(FULL, b1 ? k0 : k1, W / 4);
+#pragma unroll
+      for (int off = W / 8; off >= 1; off >>= 1) k += __shfl_xor_sync(FULL, k, off);
+      const int c = c0 + (2 * (int)b2 + (int)b1) * GR + g;
+      if ((gl & (W / 4 - 1)) == 0 && c < nc) w.ckeys[c] = make_key_nonneg((float)k, w.cids[c]);
     } else {
 #pragma unroll
       for (int u = 0; u < UNR; u++) {

@@ -195,7 +195,7 @@ __device__ __forceinline__ void apply_set(SearchArgs& la, const SetDesc& d, int6
 }
 
 template <int DT, int METRIC, int W, int CPL, bool BATCHED>
-__global__ void __launch_bounds__(256, (BATCHED || CPL >= 3) ? 4 : 5) k_search(SearchArgs a) {
+__global__ void __launch_bounds__(256, (BATCHED || CPL >= 3 || DT == DT_U8) ? 4 : 5) k_search(SearchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpSmem w = carve(smem + (size_t)wib * a.warp_bytes, a);
