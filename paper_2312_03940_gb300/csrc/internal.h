@@ -37,7 +37,8 @@ struct SearchArgs {
   int nS;
   int Lw;             // beam width
   int log2h;          // seen-filter size: (1 << log2h) 32-bit words
-  int hash16;         // set by launch_search: the filter holds 2 << log2h 16-bit tags
+  int tag_bytes;      // set by launch_search: the filter holds (4 / tag_bytes) << log2h
+                     // tags of 1, 2 or 4 (the whole id) bytes
   int stage;          // candidate staging entries per warp (>= max(R, nS))
   int vcap;           // BUILD: visited points kept
   int mode;

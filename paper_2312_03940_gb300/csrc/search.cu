@@ -73,9 +73,11 @@ cudaError_t launch_search_batched(const DataView& dv, const SearchArgs& a, const
 
 cudaError_t launch_search(const DataView& dv, SearchArgs a, cudaStream_t st) {
   if (a.nq <= 0 && !a.nq_dev) return cudaSuccess;
-  // 16-bit tags when every id splits into slot bits and a tag below 0xffff
-  // (0xffff marks an empty slot); in a batched launch a.n is the largest set
-  a.hash16 = ((uint64_t)(a.n - 1) >> (a.log2h + 1)) < 0xffffu ? 1 : 0;
+  // the narrowest tags for which every id splits into slot bits and a tag
+  // below the all-ones empty marker (8-bit: 4x the slots of whole ids in the
+  // same bytes); in a batched launch a.n is the largest set
+  const uint64_t top = (uint64_t)(a.n - 1);
+  a.tag_bytes = (top >> (a.log2h + 2)) < 0xffu ? 1 : ((top >> (a.log2h + 1)) < 0xffffu ? 2 : 4);
   Layout L;
   if (!pick_layout(dv.dtype, dv.metric, dv.d, &L)) return cudaErrorNotSupported;
   if (a.sets) return launch_search_batched(dv, a, L, st);

@@ -47,9 +47,17 @@ __device__ __forceinline__ int admit(const SearchArgs& a, WarpSmem& w, int32_t y
     if (y >= a.n) {
       set_error(a.err, ERR_BAD_ID);
     } else if (y != q) {
-      if (a.hash16) {
-        // twice the slots in the same bytes: slot = low id bits, tag = the
-        // remaining high bits, so a match still means exactly this id
+      // narrow tags: more slots in the same bytes; slot = low id bits, tag =
+      // the remaining high bits, so a match still means exactly this id
+      if (a.tag_bytes == 1) {
+        uint8_t* h8 = reinterpret_cast<uint8_t*>(w.hash);
+        const uint32_t s = (uint32_t)y & ((4u << a.log2h) - 1);
+        const uint8_t tag = (uint8_t)((uint32_t)y >> (a.log2h + 2));
+        if (h8[s] != tag) {
+          h8[s] = tag;
+          take = true;
+        }
+      } else if (a.tag_bytes == 2) {
         uint16_t* h16 = reinterpret_cast<uint16_t*>(w.hash);
         const uint32_t s = (uint32_t)y & ((2u << a.log2h) - 1);
         const uint16_t tag = (uint16_t)((uint32_t)y >> (a.log2h + 1));

@@ -23,7 +23,10 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
   for (int i = lane; i < H; i += 32) w.hash[i] = -1;
   __syncwarp();
   if (lane == 0) {
-    if (a.hash16)
+    if (a.tag_bytes == 1)
+      reinterpret_cast<uint8_t*>(w.hash)[(uint32_t)q & ((4u << a.log2h) - 1)] =
+          (uint8_t)((uint32_t)q >> (a.log2h + 2));
+    else if (a.tag_bytes == 2)
       reinterpret_cast<uint16_t*>(w.hash)[(uint32_t)q & ((2u << a.log2h) - 1)] =
           (uint16_t)((uint32_t)q >> (a.log2h + 1));
     else
