@@ -38,65 +38,66 @@ __device__ __forceinline__ WarpSmem carve(uint8_t* base, const SearchArgs& a) {
   return w;
 }
 
-// Admit id y as a new candidate unless it is padding, the query or already
-// evaluated (as far as the filter remembers). Collective over the warp.
+// Admit id y as a new candidate unless it is padding (< 0), the query or
+// already evaluated (as far as the filter remembers); an id >= n is skipped
+// and noted in *bad. TB: tag bytes of the filter (1 or 2: slot = low id bits,
+// tag = the remaining high bits, so a match still means exactly this id; 4:
+// whole ids at a hashed slot). Every slot index is masked, so the table
+// lookups stay in bounds for any y and need no branch. Collective.
+template <int TB>
 __device__ __forceinline__ int admit(const SearchArgs& a, WarpSmem& w, int32_t y, int32_t q, int nc,
-                                     int lane) {
-  bool take = false;
-  if (y >= 0) {
-    if (y >= a.n) {
-      set_error(a.err, ERR_BAD_ID);
-    } else if (y != q) {
-      // narrow tags: more slots in the same bytes; slot = low id bits, tag =
-      // the remaining high bits, so a match still means exactly this id
-      if (a.tag_bytes == 1) {
-        uint8_t* h8 = reinterpret_cast<uint8_t*>(w.hash);
-        const uint32_t s = (uint32_t)y & ((4u << a.log2h) - 1);
-        const uint8_t tag = (uint8_t)((uint32_t)y >> (a.log2h + 2));
-        if (h8[s] != tag) {
-          h8[s] = tag;
-          take = true;
-        }
-      } else if (a.tag_bytes == 2) {
-        uint16_t* h16 = reinterpret_cast<uint16_t*>(w.hash);
-        const uint32_t s = (uint32_t)y & ((2u << a.log2h) - 1);
-        const uint16_t tag = (uint16_t)((uint32_t)y >> (a.log2h + 1));
-        if (h16[s] != tag) {
-          h16[s] = tag;
-          take = true;
-        }
-      } else {
-        uint32_t s = hash_slot(y, a.log2h);
-        if (w.hash[s] != y) {
-          w.hash[s] = y;
-          take = true;
-        }
-      }
-    }
+                                     unsigned lt, bool* bad) {
+  const bool cand = ((uint32_t)y < (uint32_t)a.n) & (y != q);
+  *bad |= y >= a.n;
+  bool take;
+  if constexpr (TB == 1) {
+    uint8_t* h = reinterpret_cast<uint8_t*>(w.hash);
+    const uint32_t s = (uint32_t)y & ((4u << a.log2h) - 1);
+    const uint8_t tag = (uint8_t)((uint32_t)y >> (a.log2h + 2));
+    take = cand & (h[s] != tag);
+    if (take) h[s] = tag;
+  } else if constexpr (TB == 2) {
+    uint16_t* h = reinterpret_cast<uint16_t*>(w.hash);
+    const uint32_t s = (uint32_t)y & ((2u << a.log2h) - 1);
+    const uint16_t tag = (uint16_t)((uint32_t)y >> (a.log2h + 1));
+    take = cand & (h[s] != tag);
+    if (take) h[s] = tag;
+  } else {
+    const uint32_t s = hash_slot(y, a.log2h);
+    take = cand & (w.hash[s] != y);
+    if (take) w.hash[s] = y;
   }
-  unsigned m = __ballot_sync(FULL, take);
-  if (take) w.cids[nc + __popc(m & lanemask_lt())] = y;
+  const unsigned m = __ballot_sync(FULL, take);
+  if (take) w.cids[nc + __popc(m & lt)] = y;
   return nc + __popc(m);
 }
 
 // Candidate ids from the out-list of p.
-__device__ __forceinline__ int gather_out(const SearchArgs& a, WarpSmem& w, int32_t p, int32_t q,
-                                          int lane) {
+template <int TB>
+__device__ __forceinline__ int gather_out_t(const SearchArgs& a, WarpSmem& w, int32_t p, int32_t q, int lane,
+                                            unsigned lt, bool* bad) {
   const int32_t* row = a.G + wide_mul(p, a.R);
   int nc = 0;
   for (int b = 0; b < a.R; b += 32) {
-    int idx = b + lane;
-    int32_t y = idx < a.R ? __ldg(row + idx) : -1;
-    nc = admit(a, w, y, q, nc, lane);
+    const int idx = b + lane;
+    const int32_t y = idx < a.R ? __ldg(row + idx) : -1;
+    nc = admit<TB>(a, w, y, q, nc, lt, bad);
   }
   __syncwarp();
   return nc;
 }
 
+__device__ __forceinline__ int gather_out(const SearchArgs& a, WarpSmem& w, int32_t p, int32_t q, int lane,
+                                          unsigned lt, bool* bad) {
+  if (a.tag_bytes == 1) return gather_out_t<1>(a, w, p, q, lane, lt, bad);
+  if (a.tag_bytes == 2) return gather_out_t<2>(a, w, p, q, lane, lt, bad);
+  return gather_out_t<4>(a, w, p, q, lane, lt, bad);
+}
+
 // Candidate ids from the start points S[s0 .. s0 + stage); *q_in_s is set
 // when the query itself is one of them.
 __device__ __forceinline__ int gather_start(const SearchArgs& a, WarpSmem& w, int32_t q, int s0, int lane,
-                                            bool* q_in_s) {
+                                            unsigned lt, bool* bad, bool* q_in_s) {
   int nc = 0;
   bool has_q = false;
   const int s1 = min(a.nS, s0 + a.stage);
@@ -104,7 +105,12 @@ __device__ __forceinline__ int gather_start(const SearchArgs& a, WarpSmem& w, in
     int idx = b + lane;
     int32_t y = idx < s1 ? __ldg(a.S + idx) : -1;
     has_q |= __any_sync(FULL, y == q);
-    nc = admit(a, w, y, q, nc, lane);
+    if (a.tag_bytes == 1)
+      nc = admit<1>(a, w, y, q, nc, lt, bad);
+    else if (a.tag_bytes == 2)
+      nc = admit<2>(a, w, y, q, nc, lt, bad);
+    else
+      nc = admit<4>(a, w, y, q, nc, lt, bad);
   }
   __syncwarp();
   *q_in_s |= has_q;

@@ -41,10 +41,12 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
   // chunks; keeping the Lw closest of each merge leaves the Lw closest
   // points of S, which is what the first prune of Algorithm 1 keeps.
   bool q_in_s = a.S == nullptr;
+  bool bad = false;  // an id >= n in S or an out-list (reported once below)
+  const unsigned lt = lanemask_lt();
   int nc = 0;
   int64_t evals = 0;
   for (int s0 = 0; a.S && s0 < a.nS; s0 += a.stage) {
-    nc = gather_start(a, w, q, s0, lane, &q_in_s);
+    nc = gather_start(a, w, q, s0, lane, lt, &bad, &q_in_s);
     if (nc) {
       eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
       merge_cands(w, nb, a.Lw, nc, cursor, lane);
@@ -53,7 +55,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
   }
   int64_t iters = 0;
   if (q_in_s) {
-    nc = gather_out(a, w, q, q, lane);
+    nc = gather_out(a, w, q, q, lane, lt, &bad);
     iters = 1;
     if (nc) {
       eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
@@ -77,7 +79,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
     const int32_t p = key_id(e);
     if (a.mode == MODE_BUILD) record_visit(w, nv, a.vcap, key_clean(e), lane);
     // L <- L u E_out(p*), keeping the Lw closest
-    nc = gather_out(a, w, p, q, lane);
+    nc = gather_out(a, w, p, q, lane, lt, &bad);
     if (nc) {
       eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
       merge_cands(w, nb, a.Lw, nc, cursor, lane);
@@ -88,6 +90,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
       break;
     }
   }
+  if (__any_sync(FULL, bad) && lane == 0) set_error(a.err, ERR_BAD_ID);
   if (a.work && lane == 0) {
     atomicAdd(a.work, (unsigned long long)iters);
     atomicAdd(a.work + 1, (unsigned long long)evals);
