@@ -491,7 +491,8 @@ def run_batched64(args):
 
 
 def run_reduced(args, kind):
-    """FP32 traversal vs BF16 traversal (exact FP32 re-rank) on the same graph."""
+    """FP32 traversal vs BF16 (and, for inner product, FP8 e4m3 with per-dimension
+    scales) traversal with exact FP32 re-rank, on the same graph."""
     import torch
 
     from oracle import exact
@@ -516,6 +517,12 @@ def run_reduced(args, kind):
     Xb = Xd.to(torch.bfloat16).contiguous()
     ds32 = pc.Dataset(Xd, metric=metric)
     dsb = pc.Dataset(Xb, metric=metric, data_f32=Xd)
+    variants = [("fp32", ds32), ("bf16", dsb)]
+    if metric == pc.IP:
+        # s_j = max_i |x_ij| / 448 (the largest e4m3 value); codes of x / s
+        scale = (Xd.abs().amax(0) / 448.0).clamp_min(torch.finfo(torch.float32).tiny).contiguous()
+        variants.append(("fp8", pc.Dataset((Xd / scale).to(torch.float8_e4m3fn).contiguous(), metric=metric,
+                                           dim_scale=scale, data_f32=Xd)))
     p = pc.params(k=k, R=R, L_build=2 * L, L_search=L, L_dep=L, alpha=alpha, build_passes=2,
                   n_start=max(16, min(n, 8192 * n // 1_000_000)), n_clusters=ncl)
     t0 = time.perf_counter()
@@ -528,7 +535,7 @@ def run_reduced(args, kind):
     res = {}
     for name, fn in dens_fns:
         p.density = fn
-        for tag, ds in (("fp32", ds32), ("bf16", dsb)):
+        for tag, ds in variants:
             ws = pc.workspace(ds, p)
             out = {}
 
@@ -549,7 +556,9 @@ def run_reduced(args, kind):
                                     "recall": exact.knn_recall(out["knn_dist"][torch.from_numpy(qs).cuda()].cpu().numpy(),
                                                                ex),
                                     "labels": out["labels"].cpu().numpy()}
-        res[f"{name}/bf16"]["ari_vs_fp32"] = exact.ari(res[f"{name}/bf16"]["labels"], res[f"{name}/fp32"]["labels"])
+        for tag, _ in variants[1:]:
+            res[f"{name}/{tag}"]["ari_vs_fp32"] = exact.ari(res[f"{name}/{tag}"]["labels"],
+                                                             res[f"{name}/fp32"]["labels"])
     for v in res.values():
         v.pop("labels")
     print(json.dumps({"workload": kind, "config": {"workload": desc, "build_s": build_s}, "results": res}),

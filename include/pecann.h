@@ -31,15 +31,20 @@
  *  - Point rows are n x d, row-major, contiguous, 16-byte aligned. d must be
  *    a multiple of 4 (FP32), 8 (BF16) or 16 (U8, FP8). U8 supports the L2
  *    metric with d <= 256 (so that every distance is an exact integer in FP32).
- *  - Reduced-precision traversal: a BF16 dataset must also give data_f32,
- *    the same points in FP32. Graph searches walk the BF16 rows (FP32
- *    accumulation); every distance that leaves the library (k-NN lists,
+ *  - Reduced-precision traversal: a BF16 or FP8 dataset must also give
+ *    data_f32, the same points in FP32. Graph searches walk the BF16 / FP8
+ *    rows (FP32 accumulation); every distance that leaves the library (k-NN lists,
  *    densities, dependent distances) is recomputed exactly on the FP32 rows
  *    for the candidates the traversal found: the k-NN search hands its
  *    rerank_k best points, each dependent round its first 32 points ranked
  *    above the query. Graph builds, brute-force fallbacks and the
- *    brute-force tail use the FP32 rows. FP8 traversal has no kernel yet
- *    (PECANN_EUNSUPPORTED).
+ *    brute-force tail use the FP32 rows.
+ *  - FP8 (e4m3) rows hold codes of x_j / s_j with per-dimension scales
+ *    dim_scale (d floats, 16-byte aligned; e.g. s_j = max_i |x_ij| / 448, the
+ *    largest e4m3 value), so the decoded point is x_j = s_j * code_j. FP8
+ *    traversal supports the IP metric (the scale folds into the query: the
+ *    traversal scores 1 - sum_j (q_j s_j) code_j with q from data_f32, d up
+ *    to 1024); L2 on FP8 rows returns PECANN_EUNSUPPORTED.
  *  - Distances: the library orders points by the FP32 "dissimilarity" dis --
  *    the squared Euclidean distance (L2) or 1 - <x, y> (IP, unit-norm rows) --
  *    summed in one fixed order: 4-element chunk c of a row is accumulated with
@@ -135,7 +140,8 @@ typedef struct {
   int32_t dtype;          /* pecann_dtype                                        */
   int32_t metric;         /* pecann_metric                                       */
   int32_t reserved0;
-  const float* dim_scale; /* FP8 only: device, d per-dimension scales (x = q * s) */
+  const float* dim_scale; /* FP8 only: device, d per-dimension scales
+                             (decoded x_j = dim_scale[j] * code_j)               */
   const float* data_f32;  /* BF16/FP8 only: device n x d FP32 rows for the exact
                              re-rank; NULL for FP32/U8 data                      */
 } pecann_dataset;

@@ -83,6 +83,12 @@ static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataV
   if (((uintptr_t)ds->data) & 15) return set_last_error("rows must be 16-byte aligned"), PECANN_EINVAL;
   if (is_reduced(ds->dtype) && (!ds->data_f32 || (((uintptr_t)ds->data_f32) & 15)))
     return set_last_error("BF16 / FP8 data needs 16-byte aligned FP32 rows in data_f32"), PECANN_EINVAL;
+  if (ds->dtype == DT_FP8) {
+    if (!ds->dim_scale || (((uintptr_t)ds->dim_scale) & 15))
+      return set_last_error("FP8 data needs a 16-byte aligned dim_scale array of d floats"), PECANN_EINVAL;
+    if (ds->metric != MET_IP)
+      return set_last_error("FP8 traversal supports the inner-product metric only"), PECANN_EUNSUPPORTED;
+  }
   Layout L;
   if (!pick_layout(ds->dtype, ds->metric, ds->d, &L))
     return set_last_error("no kernel for this dtype / metric / d"), PECANN_EUNSUPPORTED;
@@ -95,6 +101,8 @@ static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataV
   dv->metric = ds->metric;
   dv->row_bytes = (int64_t)ds->d * elem_bytes(ds->dtype);
   dv->C = (int)(dv->row_bytes / 16);
+  dv->f32_rows = ds->dtype == DT_FP8 ? ds->data_f32 : nullptr;
+  dv->scale = ds->dtype == DT_FP8 ? ds->dim_scale : nullptr;
   if (f32) {
     *f32 = *dv;
     if (is_reduced(ds->dtype)) {

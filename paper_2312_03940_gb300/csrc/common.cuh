@@ -209,6 +209,37 @@ struct Partial<DT_BF16, MET_IP, CPL> {
   }
 };
 
+// FP8 e4m3 rows, inner product: decoded x_j = s_j * code_j, and the query
+// side carries a_j = q_j * s_j (FP32), so the dot product is sum a_j code_j
+// with one decode and one FMA per element. q holds four FP32 chunks (16
+// values) per 16-byte row chunk.
+__device__ __forceinline__ float2 e4m3x2_to_f2(unsigned v) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(v & 0xffffu), __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2*>(&h));
+}
+
+template <int CPL>
+struct Partial<DT_FP8, MET_IP, CPL> {
+  typedef float acc_t;
+  __device__ __forceinline__ static float run(const uint4 (&q)[4 * CPL], const uint4 (&r)[CPL]) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < CPL; t++) {
+      const unsigned ra[4] = {r[t].x, r[t].y, r[t].z, r[t].w};
+#pragma unroll
+      for (int w = 0; w < 4; w++) {
+        const uint4 qq = q[4 * t + w];
+        const float2 lo = e4m3x2_to_f2(ra[w]), hi = e4m3x2_to_f2(ra[w] >> 16);
+        acc = __fmaf_rn(__uint_as_float(qq.x), lo.x, acc);
+        acc = __fmaf_rn(__uint_as_float(qq.y), lo.y, acc);
+        acc = __fmaf_rn(__uint_as_float(qq.z), hi.x, acc);
+        acc = __fmaf_rn(__uint_as_float(qq.w), hi.y, acc);
+      }
+    }
+    return acc;
+  }
+};
+
 // Butterfly over a group of W lanes (every lane ends with the same value).
 template <int W>
 __device__ __forceinline__ float group_sum(float v) {
@@ -225,8 +256,8 @@ __device__ __forceinline__ unsigned group_sum(unsigned v) {
 
 // Dissimilarity of the group's row to the query (collective over the warp;
 // every lane of the group gets the value).
-template <int DT, int METRIC, int W, int CPL>
-__device__ __forceinline__ float group_dis(const uint4 (&q)[CPL], const uint4 (&r)[CPL]) {
+template <int DT, int METRIC, int W, int CPL, int QC>
+__device__ __forceinline__ float group_dis(const uint4 (&q)[QC], const uint4 (&r)[CPL]) {
   auto part = Partial<DT, METRIC, CPL>::run(q, r);
   auto s = group_sum<W>(part);
   if (METRIC == MET_L2) return (float)s;

@@ -76,6 +76,10 @@ struct SearchArgs {
   const int32_t* nq_dev;
   const int32_t* set_active;  // batched dependent rounds: sets still doubling (NULL: all)
   int64_t id_base;           // global id of the set's point 0 (0 outside batches)
+  // FP8 rows: the query is taken from its FP32 row times the per-dimension
+  // scale (set by launch_search from the DataView)
+  const float* qrows;        // n x d FP32 rows
+  const float* scale;        // d scales: decoded x_j = scale_j * code_j
 };
 
 struct DataView {
@@ -86,6 +90,8 @@ struct DataView {
   int metric;
   int64_t row_bytes;
   int C;  // 16-byte chunks
+  const float* f32_rows = nullptr;  // FP8 only: the FP32 rows (query side of the traversal)
+  const float* scale = nullptr;     // FP8 only: d per-dimension scales
 };
 
 // Distance-kernel layout for a dataset: W lanes per row, CPL chunks per lane.

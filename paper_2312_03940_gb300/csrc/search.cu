@@ -34,9 +34,21 @@ int search_warp_bytes(int Lw, int log2h, int stage, int vcap, bool build) {
 bool pick_layout(int dtype, int metric, int d, Layout* out) {
   int epc = dtype == DT_F32 ? 4 : (dtype == DT_BF16 ? 8 : 16);
   if (d <= 0 || d % epc) return false;
+  if (dtype != DT_F32 && dtype != DT_U8 && dtype != DT_BF16 && dtype != DT_FP8) return false;
   if (dtype == DT_U8 && (metric != MET_L2 || d > 256)) return false;
-  if (dtype == DT_FP8) return false;  // FP8 traversal has no kernel in this build
   int C = d / epc;
+  if (dtype == DT_FP8) {
+    // inner product only: the scale folds into the query (a_j = q_j s_j), so
+    // a row costs one decode and one FMA per element; L2 would need s_j^2 per
+    // element as a second operand
+    if (metric != MET_IP) return false;
+    if (C <= 8) *out = {8, 1};
+    else if (C <= 16) *out = {16, 1};
+    else if (C <= 32) *out = {32, 1};
+    else if (C <= 64) *out = {32, 2};  // d <= 1024, the FP32 re-rank's limit
+    else return false;
+    return true;
+  }
   if (dtype == DT_U8) {
     // integer sums are exact in any order; one 16-byte chunk per lane (a
     // 128-byte row takes 8 lanes) measured faster than two chunks per lane
@@ -70,6 +82,7 @@ cudaError_t launch_search_f32_l2(const DataView& dv, const SearchArgs& a, const 
 cudaError_t launch_search_f32_ip(const DataView& dv, const SearchArgs& a, const Layout& L, cudaStream_t st);
 cudaError_t launch_search_bf16(const DataView& dv, const SearchArgs& a, const Layout& L, cudaStream_t st);
 cudaError_t launch_search_batched(const DataView& dv, const SearchArgs& a, const Layout& L, cudaStream_t st);
+cudaError_t launch_search_fp8(const DataView& dv, const SearchArgs& a, const Layout& L, cudaStream_t st);
 
 cudaError_t launch_search(const DataView& dv, SearchArgs a, cudaStream_t st) {
   if (a.nq <= 0 && !a.nq_dev) return cudaSuccess;
@@ -83,6 +96,12 @@ cudaError_t launch_search(const DataView& dv, SearchArgs a, cudaStream_t st) {
   if (a.sets) return launch_search_batched(dv, a, L, st);
   if (dv.dtype == DT_U8) return launch_search_u8(dv, a, L, st);
   if (dv.dtype == DT_BF16) return launch_search_bf16(dv, a, L, st);
+  if (dv.dtype == DT_FP8) {
+    if (a.sets || !dv.f32_rows || !dv.scale) return cudaErrorNotSupported;
+    a.qrows = dv.f32_rows;
+    a.scale = dv.scale;
+    return launch_search_fp8(dv, a, L, st);
+  }
   if (dv.dtype == DT_F32 && dv.metric == MET_L2) return launch_search_f32_l2(dv, a, L, st);
   if (dv.dtype == DT_F32 && dv.metric == MET_IP) return launch_search_f32_ip(dv, a, L, st);
   return cudaErrorNotSupported;

@@ -118,9 +118,9 @@ __device__ __forceinline__ int gather_start(const SearchArgs& a, WarpSmem& w, in
 }
 
 // Keys (canonical distance to the query, id) of the staged candidates.
-template <int DT, int METRIC, int W, int CPL>
+template <int DT, int METRIC, int W, int CPL, int QC>
 __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int nc,
-                                           const uint4 (&qv)[CPL], int lane) {
+                                           const uint4 (&qv)[QC], int lane) {
   constexpr int GR = 32 / W;
   constexpr int UNR = CPL >= 4 ? 1 : (CPL == 1 ? 4 : 2);
   const int g = lane / W, gl = lane % W;

@@ -10,6 +10,29 @@
 
 namespace pecann {
 
+// Query side of an FP8 (inner product) row: lane gl's chunks c = gl + W t
+// hold a_j = q_j * s_j for the 16 dimensions of row chunk c, from the FP32
+// row of q and the per-dimension scales.
+template <int W, int CPL>
+__device__ __forceinline__ void load_query_fp8(const SearchArgs& a, int32_t q, int gl, uint4 (&qv)[4 * CPL]) {
+  const float4* qr = reinterpret_cast<const float4*>(a.qrows) + wide_mul(q, (int64_t)a.C * 4);
+  const float4* sc = reinterpret_cast<const float4*>(a.scale);
+#pragma unroll
+  for (int t = 0; t < CPL; t++) {
+    const int c = gl + W * t;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c < a.C) {
+        const float4 x = __ldg(qr + 4 * c + u), s = __ldg(sc + 4 * c + u);
+        v = make_float4(x.x * s.x, x.y * s.y, x.z * s.z, x.w * s.w);
+      }
+      qv[4 * t + u] = make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
+                                 __float_as_uint(v.w));
+    }
+  }
+}
+
 template <int DT, int METRIC, int W, int CPL>
 __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int64_t qi, int32_t q, int lane) {
   const int H = 1 << a.log2h;
@@ -18,8 +41,11 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
     if (lane == 0) set_error(a.err, ERR_BAD_ID);
     return;
   }
-  uint4 qv[CPL];
-  load_row<W, CPL, false>(a.X + wide_mul(q, a.row_bytes), gl, a.C, qv);
+  uint4 qv[DT == DT_FP8 ? 4 * CPL : CPL];
+  if constexpr (DT == DT_FP8)
+    load_query_fp8<W, CPL>(a, q, gl, qv);
+  else
+    load_row<W, CPL, false>(a.X + wide_mul(q, a.row_bytes), gl, a.C, qv);
   for (int i = lane; i < H; i += 32) w.hash[i] = -1;
   __syncwarp();
   if (lane == 0) {
@@ -201,7 +227,7 @@ __device__ __forceinline__ void apply_set(SearchArgs& la, const SetDesc& d, int6
 }
 
 template <int DT, int METRIC, int W, int CPL, bool BATCHED>
-__global__ void __launch_bounds__(256, (BATCHED || CPL >= 3 || DT == DT_U8) ? 4 : 5) k_search(SearchArgs a) {
+__global__ void __launch_bounds__(256, DT == DT_FP8 ? (CPL >= 2 ? 2 : 4) : ((BATCHED || CPL >= 3 || DT == DT_U8) ? 4 : 5)) k_search(SearchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpSmem w = carve(smem + (size_t)wib * a.warp_bytes, a);

@@ -43,3 +43,14 @@ def random_graph(n: int, R: int, seed: int) -> np.ndarray:
 
 def ranks_above(key, j, i):
     return key[j] > key[i] or (key[j] == key[i] and j < i)
+
+
+def quantize_e4m3(X: np.ndarray):
+    """FP8 e4m3 codes of X / s with the per-dimension scale s_j = max_i |x_ij| / 448
+    (448 is the largest e4m3 value); the decoded point is s_j * code_j.
+    Returns (codes as a torch float8_e4m3fn CPU tensor, s as float32)."""
+    import torch
+    s = (np.abs(X).max(0) / 448.0).astype(np.float32)
+    s[s == 0] = 1.0
+    codes = torch.from_numpy((X.astype(np.float32) / s).astype(np.float32)).to(torch.float8_e4m3fn)
+    return codes, s

@@ -15,6 +15,8 @@ from oracle import exact
 from paper_2312_03940_gb300 import pecann as pc
 from paper_2312_03940_gb300 import synth
 
+from tests.helpers import quantize_e4m3, random_graph
+
 pytestmark = pytest.mark.gpu
 
 
@@ -41,7 +43,7 @@ def recall_vs(ref_dist, got_dist):
     return float((got_dist <= kth * (1 + 1e-5) + 1e-30).mean())
 
 
-@pytest.mark.parametrize("kind", ["l2-384", "ip-1024"])
+@pytest.mark.parametrize("kind", ["l2-384", "ip-1024", "fp8-ip-1024"])
 def test_bf16_traversal_matches_fp32(kind):
     if kind == "l2-384":
         X, gt = synth.powerlaw_sphere(n=20000, d=384, components=200, seed=81)
@@ -52,13 +54,16 @@ def test_bf16_traversal_matches_fp32(kind):
         metric, k, R, L, nc = pc.IP, 16, 64, 128, 100
         density = pc.DENS_KTH
     Xd = torch.from_numpy(X).cuda()
-    Xb = Xd.to(torch.bfloat16).contiguous()
     p = pc.params(k=k, R=R, L_build=L, L_search=L, L_dep=L, alpha=1.2, n_start=256, build_passes=2,
                   n_clusters=nc, density=density)
     ds32 = pc.Dataset(Xd, metric=metric)
-    dsb = pc.Dataset(Xb, metric=metric, data_f32=Xd)
+    if kind.startswith("fp8"):
+        codes, s = quantize_e4m3(X)
+        dsb = pc.Dataset(codes.cuda(), metric=metric, dim_scale=torch.from_numpy(s).cuda(), data_f32=Xd)
+    else:
+        dsb = pc.Dataset(Xd.to(torch.bfloat16).contiguous(), metric=metric, data_f32=Xd)
     G, _ = pc.pecann_build_graph(ds32, p, order=torch.from_numpy(synth.insertion_order(len(X), seed=83)).cuda())
-    # a BF16 dataset builds on its FP32 rows: the same graph
+    # a BF16 / FP8 dataset builds on its FP32 rows: the same graph
     Gb, _ = pc.pecann_build_graph(dsb, p, order=torch.from_numpy(synth.insertion_order(len(X), seed=83)).cuda())
     assert torch.equal(G, Gb)
     r32 = run(ds32, G, p)
@@ -91,3 +96,51 @@ def test_bf16_requires_fp32_rows():
     with pytest.raises(pc.PecannError) as e:
         pc.pecann_density(ds, G, p, ws=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
     assert e.value.status == pc.EINVAL
+
+
+@pytest.mark.parametrize("d", [128, 256, 512, 1024])
+def test_fp8_traversal_distances(d):
+    """The FP8 traversal scores 1 - sum_j (q_j s_j) code_j: checked against a
+    CPU decode of the same codes (torch's float8 -> float32) and an FP64 dot
+    product. FP32 rounding of the d products and sums (d/32 + 6 steps on a
+    lane's path, terms summing to about 1 in magnitude) stays far below
+    1e-5 for d <= 1024."""
+    n, R, L, k = 3000, 16, 48, 12
+    X, _ = synth.vmf_like(n=n, d=d, components=20, seed=90 + d // 128)
+    codes, s = quantize_e4m3(X)
+    G = random_graph(n, R, seed=91)
+    ds = pc.Dataset(codes.cuda(), metric=pc.IP, dim_scale=torch.from_numpy(s).cuda(),
+                    data_f32=torch.from_numpy(X).cuda())
+    qs = synth.sample_ids(n, 64, seed=92).astype(np.int32)
+    ids, dis, cnt = pc.pecann_search(ds, torch.from_numpy(G).cuda(), torch.from_numpy(qs).cuda(), L=L, k=k)
+    ids, dis, cnt = ids.cpu().numpy(), dis.cpu().numpy(), cnt.cpu().numpy()
+    dec = codes.to(torch.float32).numpy().astype(np.float64) * s.astype(np.float64)
+    for r, q in enumerate(qs):
+        assert cnt[r] == k
+        assert (np.diff(dis[r]) >= 0).all()
+        ref = 1.0 - dec[ids[r]] @ X[q].astype(np.float64)
+        assert np.abs(dis[r] - ref).max() <= 1e-5, (q, np.abs(dis[r] - ref).max())
+
+
+def test_fp8_argument_checks():
+    X = np.zeros((100, 128), np.float32)
+    X[:, 0] = 1.0
+    codes, s = quantize_e4m3(X)
+    G = torch.zeros((100, 8), dtype=torch.int32, device="cuda")
+    p = pc.params(k=4, R=8, L_search=8)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    Xf = torch.from_numpy(X).cuda()
+    with pytest.raises(pc.PecannError) as e:  # L2 on FP8 rows
+        pc.pecann_density(pc.Dataset(codes.cuda(), metric=pc.L2, dim_scale=torch.from_numpy(s).cuda(),
+                                     data_f32=Xf), G, p, ws=ws)
+    assert e.value.status == pc.EUNSUPPORTED
+    with pytest.raises(pc.PecannError) as e:  # no scales
+        pc.pecann_density(pc.Dataset(codes.cuda(), metric=pc.IP, data_f32=Xf), G, p, ws=ws)
+    assert e.value.status == pc.EINVAL
+    X2 = np.zeros((100, 2048), np.float32)
+    X2[:, 0] = 1.0
+    c2, s2 = quantize_e4m3(X2)
+    with pytest.raises(pc.PecannError) as e:  # beyond the FP32 re-rank's d <= 1024
+        pc.pecann_density(pc.Dataset(c2.cuda(), metric=pc.IP, dim_scale=torch.from_numpy(s2).cuda(),
+                                     data_f32=torch.from_numpy(X2).cuda()), G, p, ws=ws)
+    assert e.value.status == pc.EUNSUPPORTED
