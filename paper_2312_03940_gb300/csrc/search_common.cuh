@@ -240,6 +240,104 @@ __device__ __forceinline__ int beam_rank(const uint64_t* beam, int nb, uint64_t 
 
 __device__ __forceinline__ int merge_filtered(WarpSmem& w, int& nb, int Lw, int m, int& cursor, int lane);
 
+__device__ __forceinline__ uint64_t min_u64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t max_u64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+// Bitonic sort (ascending) of the 32 keys x0 (position = lane) or, with TWO,
+// the 64 keys x0, x1 (positions lane and 32 + lane). Collective.
+template <bool TWO>
+__device__ __forceinline__ void warp_sort_keys(uint64_t& x0, uint64_t& x1, int lane) {
+  constexpr int NK = TWO ? 64 : 32;
+#pragma unroll
+  for (int k = 2; k <= NK; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {
+        // k = 64: positions lane and 32 + lane, one ascending run
+        const uint64_t lo = min_u64(x0, x1);
+        x1 = max_u64(x0, x1);
+        x0 = lo;
+      } else {
+        // the lower position of a pair keeps the minimum in an ascending
+        // k-block ((position & k) == 0), the maximum in a descending one
+        const bool lower = (lane & j) == 0;
+        const uint64_t y0 = __shfl_xor_sync(FULL, x0, j);
+        x0 = (lower == ((lane & k) == 0)) ? min_u64(x0, y0) : max_u64(x0, y0);
+        if (TWO) {
+          const uint64_t y1 = __shfl_xor_sync(FULL, x1, j);
+          x1 = (lower == (((lane + 32) & k) == 0)) ? min_u64(x1, y1) : max_u64(x1, y1);
+        }
+      }
+    }
+  }
+}
+
+// Merge 4..64 candidate keys (the front of ckeys, all better than the beam's
+// current Lw-th entry) into the beam: sort them in registers, drop repeats
+// (adjacent once sorted) and keys already in the beam, then merge the sorted
+// run into the beam in place. Returns the number merged. Collective.
+__device__ __forceinline__ int merge_sorted64(WarpSmem& w, int& nb, int Lw, int m, int& cursor, int lane) {
+  uint64_t x0 = lane < m ? w.ckeys[lane] : KEY_NONE;
+  uint64_t x1 = lane + 32 < m ? w.ckeys[lane + 32] : KEY_NONE;
+  if (m > 32)
+    warp_sort_keys<true>(x0, x1, lane);
+  else
+    warp_sort_keys<false>(x0, x1, lane);
+  const uint64_t up0 = __shfl_up_sync(FULL, x0, 1), up1 = __shfl_up_sync(FULL, x1, 1);
+  const uint64_t last0 = __shfl_sync(FULL, x0, 31);
+  bool ok0 = x0 != KEY_NONE && (lane == 0 || x0 != up0);
+  bool ok1 = x1 != KEY_NONE && x1 != (lane == 0 ? last0 : up1);
+  // insertion point in the old beam; a key already there is a repeat
+  int lb0 = 0, lb1 = 0;
+  if (ok0) {
+    lb0 = lower_bound_key(w.beam, nb, x0);
+    ok0 = !(lb0 < nb && key_clean(w.beam[lb0]) == x0);
+  }
+  if (ok1) {
+    lb1 = lower_bound_key(w.beam, nb, x1);
+    ok1 = !(lb1 < nb && key_clean(w.beam[lb1]) == x1);
+  }
+  const unsigned b0 = __ballot_sync(FULL, ok0), b1 = __ballot_sync(FULL, ok1);
+  const int n0 = __popc(b0), m2 = n0 + __popc(b1);
+  const unsigned lt = lanemask_lt();
+  __syncwarp();
+  if (ok0) {
+    const int r = __popc(b0 & lt);
+    w.ckeys[r] = x0;
+    w.cids[r] = lb0;
+  }
+  if (ok1) {
+    const int r = n0 + __popc(b1 & lt);
+    w.ckeys[r] = x1;
+    w.cids[r] = lb1;
+  }
+  __syncwarp();
+  if (m2 == 0) return 0;
+  const int p0 = w.cids[0];
+  // beam entries at or after p0 move up by the number of new keys below
+  // them, from the back, in place; then the new keys go to r + their point
+  for (int hi = nb - 1; hi >= p0; hi -= 32) {
+    const int idx = hi - lane;
+    uint64_t e = 0;
+    int dst = Lw;
+    if (idx >= p0) {
+      e = w.beam[idx];
+      dst = idx + count_below(w.ckeys, m2, key_clean(e));
+    }
+    __syncwarp();
+    if (dst < Lw) w.beam[dst] = e;
+    __syncwarp();
+  }
+  for (int r = lane; r < m2; r += 32) {
+    const int dst = r + w.cids[r];
+    if (dst < Lw) w.beam[dst] = w.ckeys[r];
+  }
+  __syncwarp();
+  nb = min(Lw, nb + m2);
+  if (p0 < cursor) cursor = p0;
+  return m2;
+}
+
 // Merge the staged candidate keys into the beam (keep the Lw smallest keys,
 // no duplicates). Returns the number of keys merged. Collective.
 __device__ __forceinline__ int merge_cands(WarpSmem& w, int& nb, int Lw, int nc, int& cursor, int lane) {
@@ -287,6 +385,7 @@ __device__ __forceinline__ int merge_filtered(WarpSmem& w, int& nb, int Lw, int 
     }
     return m;
   }
+  if (m <= 64) return merge_sorted64(w, nb, Lw, m, cursor, lane);
   // 2) duplicates: of an earlier survivor, or of a beam entry
   for (int i = lane; i < m; i += 32) {
     uint64_t kk = w.ckeys[i];
