@@ -82,6 +82,14 @@ __device__ __forceinline__ uint4 ldg_nc(const uint4* p) {
 
 __device__ __forceinline__ uint4 ldg_l1(const uint4* p) { return __ldg(p); }
 
+// 32 bytes from a 32-byte aligned address in one load (a 256-bit load,
+// sm_100 and later).
+__device__ __forceinline__ void ldg_nc_32b(const void* p, uint4& a, uint4& b) {
+  asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+               : "l"(p));
+}
+
 // Start moving a line into L2 without waiting for it (no register result).
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));

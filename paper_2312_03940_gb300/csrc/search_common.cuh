@@ -137,7 +137,12 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
       int c = c0 + u * GR + g;
-      if constexpr (DT == DT_U8) {
+      if constexpr (DT == DT_U8 && W == 4 && CPL == 2) {
+        // 128-byte rows at 32-byte aligned addresses: lane gl takes bytes
+        // [32 gl, 32 gl + 32) in one load, so each row line is read by one
+        // instruction
+        ldg_nc_32b(a.X + wide_mul(w.cids[min(c, nc - 1)], a.row_bytes) + 32 * gl, r[u][0], r[u][1]);
+      } else if constexpr (DT == DT_U8) {
         // a slot past the last candidate rescores the last one (discarded)
         load_row<W, CPL, true>(a.X + wide_mul(w.cids[min(c, nc - 1)], a.row_bytes), gl, a.C, r[u]);
       } else if (c < nc) {
@@ -165,6 +170,18 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
         if (gl == 0 && c < nc) w.ckeys[c] = make_key(s.x, w.cids[c]);
         if (gl == 0 && c1 < nc) w.ckeys[c1] = make_key(s.y, w.cids[c1]);
       }
+    } else if constexpr (DT == DT_U8 && UNR == 2) {
+      // the same for two rows per lane group: one split step, then plain
+      // butterfly steps; lane gl ends with row [gl & W/2]
+      const unsigned p0 = Partial<DT_U8, MET_L2, CPL>::run(qv, r[0]);
+      const unsigned p1 = Partial<DT_U8, MET_L2, CPL>::run(qv, r[1]);
+      const bool b = (gl & (W / 2)) != 0;
+      unsigned k = b ? p1 : p0;
+      k += __shfl_xor_sync(FULL, b ? p0 : p1, W / 2);
+#pragma unroll
+      for (int off = W / 4; off >= 1; off >>= 1) k += __shfl_xor_sync(FULL, k, off);
+      const int c = c0 + (int)b * GR + g;
+      if ((gl & (W / 2 - 1)) == 0 && c < nc) w.ckeys[c] = make_key_nonneg((float)k, w.cids[c]);
     } else if constexpr (DT == DT_U8 && UNR == 4) {
       // integer partials, exact in any order: reduce the group's four rows
       // together. The first two steps halve the rows a lane carries (it keeps

@@ -42,10 +42,16 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
     return;
   }
   uint4 qv[DT == DT_FP8 ? 4 * CPL : CPL];
-  if constexpr (DT == DT_FP8)
+  if constexpr (DT == DT_FP8) {
     load_query_fp8<W, CPL>(a, q, gl, qv);
-  else
+  } else if constexpr (DT == DT_U8 && W == 4 && CPL == 2) {
+    // the contiguous 32-byte lane chunks of the aligned 128-byte layout
+    const uint4* qr = reinterpret_cast<const uint4*>(a.X + wide_mul(q, a.row_bytes)) + 2 * gl;
+    qv[0] = ldg_l1(qr);
+    qv[1] = ldg_l1(qr + 1);
+  } else {
     load_row<W, CPL, false>(a.X + wide_mul(q, a.row_bytes), gl, a.C, qv);
+  }
   for (int i = lane; i < H; i += 32) w.hash[i] = -1;
   __syncwarp();
   if (lane == 0) {

@@ -100,6 +100,30 @@ def test_search_matches_oracle(dtype, d, metric):
             assert (dis[r, :cnt[r]] == od).all(), (L, qq)
 
 
+def test_u8_row_base_alignment():
+    """128-byte uint8 rows are scored by 4 lanes with one 32-byte load each
+    when the row base is 32-byte aligned, and by 8 lanes of 16 bytes
+    otherwise: both layouts give the oracle's results."""
+    n, d = 2500, 128
+    g = np.random.default_rng(77)
+    X = g.integers(0, 256, size=(n, d), dtype=np.uint8)
+    G = random_graph(n, 24, seed=77)
+    P = oracle.Points(X)
+    q = synth.sample_ids(n, 100, seed=78).astype(np.int32)
+    buf = torch.empty(n * d + 64, dtype=torch.uint8, device="cuda")
+    outs = []
+    for off in (0, 16):
+        Xv = buf[off:off + n * d].view(n, d)
+        Xv.copy_(t(X))
+        assert (Xv.data_ptr() % 32 == 0) == (off == 0)
+        ids, dis, cnt = pc.pecann_search(pc.Dataset(Xv), t(G), t(q), L=64, k=10)
+        outs.append((ids.cpu().numpy(), dis.cpu().numpy()))
+    for r, qq in enumerate(q):
+        oi, od = oracle.greedy_search(P, G, int(qq), [int(qq)], L=64, k=10)
+        for ids, dis in outs:
+            assert (ids[r] == oi).all() and (dis[r] == od).all(), qq
+
+
 @pytest.mark.parametrize("n_start", [20, 700])
 def test_search_with_start_set(n_start):
     """Start sets smaller and larger than the staging area (the larger one is
