@@ -133,6 +133,19 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
     }
   }
   for (int c0 = 0; c0 < nc; c0 += GR * UNR) {
+    if constexpr (DT == DT_U8 && W == 4 && CPL == 2) {
+      if (nc - c0 <= GR) {
+        // at most one row per lane group left: a pass of GR rows
+        const int c = c0 + g;
+        uint4 r1[2];
+        ldg_nc_32b(a.X + wide_mul(w.cids[min(c, nc - 1)], a.row_bytes) + 32 * gl, r1[0], r1[1]);
+        unsigned k = Partial<DT_U8, MET_L2, CPL>::run(qv, r1);
+        k += __shfl_xor_sync(FULL, k, 2);
+        k += __shfl_xor_sync(FULL, k, 1);
+        if (gl == 0 && c < nc) w.ckeys[c] = make_key_nonneg((float)k, w.cids[c]);
+        break;
+      }
+    }
     uint4 r[UNR][CPL];
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
