@@ -78,10 +78,19 @@ __device__ __forceinline__ int gather_out_t(const SearchArgs& a, WarpSmem& w, in
                                             unsigned lt, bool* bad) {
   const int32_t* row = a.G + wide_mul(p, a.R);
   int nc = 0;
-  for (int b = 0; b < a.R; b += 32) {
-    const int idx = b + lane;
-    const int32_t y = idx < a.R ? __ldg(row + idx) : -1;
-    nc = admit<TB>(a, w, y, q, nc, lt, bad);
+  if ((a.R & 63) == 0 && (((uintptr_t)a.G) & 7) == 0) {
+    // 8-byte aligned rows of a multiple of 64 ids: two ids per lane per load
+    for (int b = 0; b < a.R; b += 64) {
+      const int2 yy = __ldg(reinterpret_cast<const int2*>(row + b) + lane);
+      nc = admit<TB>(a, w, yy.x, q, nc, lt, bad);
+      nc = admit<TB>(a, w, yy.y, q, nc, lt, bad);
+    }
+  } else {
+    for (int b = 0; b < a.R; b += 32) {
+      const int idx = b + lane;
+      const int32_t y = idx < a.R ? __ldg(row + idx) : -1;
+      nc = admit<TB>(a, w, y, q, nc, lt, bad);
+    }
   }
   __syncwarp();
   return nc;

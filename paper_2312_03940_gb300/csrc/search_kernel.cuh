@@ -232,8 +232,22 @@ __device__ __forceinline__ void apply_set(SearchArgs& la, const SetDesc& d, int6
   if (la.delta) la.delta += base;
 }
 
+// Resident 256-thread blocks per SM that the register allocation of an
+// instance is sized for: wide query rows (FP8 with 2 chunks a lane, FP32 with
+// 8, batched FP32 with 4 or more) and BF16 (its query is held unpacked) need
+// more than 64 registers to stay free of spills; shared memory caps these at
+// 2-4 blocks anyway. (Batched FP32 with 3 chunks a lane spills a few bytes at
+// 4 blocks, which measured faster than 3 spill-free blocks.)
+template <int DT, int CPL, bool BATCHED>
+constexpr int search_min_blocks() {
+  if ((DT == DT_FP8 && CPL >= 2) || CPL >= 8 || (BATCHED && CPL >= 4)) return 2;
+  if (DT == DT_BF16) return 3;
+  if (BATCHED || CPL >= 3 || DT == DT_U8 || DT == DT_FP8) return 4;
+  return 5;
+}
+
 template <int DT, int METRIC, int W, int CPL, bool BATCHED>
-__global__ void __launch_bounds__(256, DT == DT_FP8 ? (CPL >= 2 ? 2 : 4) : ((BATCHED || CPL >= 3 || DT == DT_U8) ? 4 : 5)) k_search(SearchArgs a) {
+__global__ void __launch_bounds__(256, search_min_blocks<DT, CPL, BATCHED>()) k_search(SearchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpSmem w = carve(smem + (size_t)wib * a.warp_bytes, a);
