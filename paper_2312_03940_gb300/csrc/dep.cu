@@ -139,6 +139,86 @@ __global__ void __launch_bounds__(256) k_dep_bf(const uint8_t* X, int64_t row_by
   }
 }
 
+// DPBruteForce for uint8 rows of at most 8 16-byte chunks (d <= 128): one
+// point per thread with its row in registers, scored against a tile of up to
+// DEP_TAIL_QT queries broadcast from shared memory (integer distances: any
+// summation order is exact). A thread keeps its best key per query; warp
+// minima (two 32-bit reductions: distance bits, then id), a shared-memory
+// minimum and one atomicMin per query and block combine them.
+__global__ void __launch_bounds__(256) k_dep_bf_u8(const uint8_t* X, int64_t row_bytes, int64_t n, int C,
+                                                   const int32_t* list, int64_t m, const float* rk,
+                                                   int64_t chunk, unsigned long long* best) {
+  constexpr int CM = 8;
+  __shared__ uint4 qrows[DEP_TAIL_QT * CM];
+  __shared__ unsigned long long tile_best[DEP_TAIL_QT];
+  __shared__ int32_t tile_q[DEP_TAIL_QT];
+  __shared__ float tile_rk[DEP_TAIL_QT];
+  const int lane = threadIdx.x & 31;
+  const int64_t j0 = (int64_t)blockIdx.x * chunk;
+  const int64_t j1 = min(n, j0 + chunk);
+  for (int64_t ub = 0; ub < m; ub += DEP_TAIL_QT) {
+    const int nq = (int)(m - ub < DEP_TAIL_QT ? m - ub : DEP_TAIL_QT);
+    for (int i = threadIdx.x; i < DEP_TAIL_QT * CM; i += blockDim.x) {
+      const int qq = i / CM, c = i % CM;
+      qrows[i] = (qq < nq && c < C)
+                     ? __ldg(reinterpret_cast<const uint4*>(X + (int64_t)list[ub + qq] * row_bytes) + c)
+                     : make_uint4(0, 0, 0, 0);
+    }
+    if (threadIdx.x < DEP_TAIL_QT) {
+      tile_best[threadIdx.x] = KEY_NONE;
+      const bool live = threadIdx.x < nq;
+      tile_q[threadIdx.x] = live ? list[ub + threadIdx.x] : -1;
+      tile_rk[threadIdx.x] = live ? __ldg(rk + list[ub + threadIdx.x]) : 0.0f;
+    }
+    __syncthreads();
+    unsigned long long bq[DEP_TAIL_QT];
+#pragma unroll
+    for (int qq = 0; qq < DEP_TAIL_QT; qq++) bq[qq] = KEY_NONE;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+      const uint4* rp = reinterpret_cast<const uint4*>(X + j * row_bytes);
+      uint4 r[CM];
+#pragma unroll
+      for (int c = 0; c < CM; c++) r[c] = c < C ? __ldg(rp + c) : make_uint4(0, 0, 0, 0);
+      const float rkj = __ldg(rk + j);
+#pragma unroll
+      for (int qq = 0; qq < DEP_TAIL_QT; qq++) {
+        if (qq < nq) {
+          unsigned acc = 0;
+#pragma unroll
+          for (int c = 0; c < CM; c++) {
+            const uint4 qv = qrows[qq * CM + c];
+            const unsigned a0 = __vabsdiffu4(qv.x, r[c].x), a1 = __vabsdiffu4(qv.y, r[c].y);
+            const unsigned a2 = __vabsdiffu4(qv.z, r[c].z), a3 = __vabsdiffu4(qv.w, r[c].w);
+            acc = __dp4a(a0, a0, acc);
+            acc = __dp4a(a1, a1, acc);
+            acc = __dp4a(a2, a2, acc);
+            acc = __dp4a(a3, a3, acc);
+          }
+          const int32_t q = tile_q[qq];
+          const float rkq = tile_rk[qq];
+          // j ranks above q: larger key, or equal key and smaller id
+          if (j != q && (rkj > rkq || (rkj == rkq && j < q))) {
+            const unsigned long long kk = make_key((float)acc, (int32_t)j);
+            bq[qq] = kk < bq[qq] ? kk : bq[qq];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int qq = 0; qq < DEP_TAIL_QT; qq++) {
+      if (qq < nq) {
+        const uint32_t hi = (uint32_t)(bq[qq] >> 32);
+        const uint32_t mh = __reduce_min_sync(FULL, hi);
+        const uint32_t ml = __reduce_min_sync(FULL, hi == mh ? (uint32_t)bq[qq] : 0xffffffffu);
+        if (lane == 0 && mh != 0xffffffffu) atomicMin(tile_best + qq, ((unsigned long long)mh << 32) | ml);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nq && tile_best[threadIdx.x] != KEY_NONE) atomicMin(best + ub + threadIdx.x, tile_best[threadIdx.x]);
+    __syncthreads();
+  }
+}
+
 __global__ void k_fill_u64(unsigned long long* p, int64_t m, unsigned long long v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -181,10 +261,22 @@ cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int
   Layout L;
   if (!pick_layout(dv.dtype, dv.metric, dv.d, &L)) return cudaErrorNotSupported;
   k_fill_u64<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(best, m, KEY_NONE); note_launch();
-  cudaError_t e = dispatch_layout(dv, [&](auto dt, auto met, auto wv, auto cpl) -> cudaError_t {
-    return launch_dep_bf_inst<decltype(dt)::value, decltype(met)::value, decltype(wv)::value,
-                              decltype(cpl)::value>(dv, d_list, m, rank_key, best, st);
-  });
+  cudaError_t e;
+  if (dv.dtype == DT_U8 && dv.C <= 8) {
+    // one point per thread: about two blocks per SM fit its registers
+    const int64_t blocks_target = (int64_t)num_sms() * 2;
+    int64_t chunk = (dv.n + blocks_target - 1) / blocks_target;
+    if (chunk < 256) chunk = 256;
+    const int64_t grid = (dv.n + chunk - 1) / chunk;
+    k_dep_bf_u8<<<(unsigned)grid, 256, 0, st>>>(dv.X, dv.row_bytes, dv.n, dv.C, d_list, m, rank_key, chunk, best);
+    note_launch();
+    e = cudaGetLastError();
+  } else {
+    e = dispatch_layout(dv, [&](auto dt, auto met, auto wv, auto cpl) -> cudaError_t {
+      return launch_dep_bf_inst<decltype(dt)::value, decltype(met)::value, decltype(wv)::value,
+                                decltype(cpl)::value>(dv, d_list, m, rank_key, best, st);
+    });
+  }
   if (e != cudaSuccess) return e;
   k_dep_bf_finish<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(d_list, m, best, dv.metric, lam, delta); note_launch();
   return cudaGetLastError();

@@ -263,6 +263,27 @@ def test_fallback_and_tail_paths():
     assert r["stats"][63] == d["tail"]
 
 
+@pytest.mark.parametrize("d", [128, 64])
+def test_u8_tail(d):
+    """uint8 rows of up to 128 bytes take the one-point-per-thread brute-force
+    tail (d = 64 leaves half the chunks empty); a zero threshold and a
+    one-round cap send hundreds of points there. Ties are frequent (coarse
+    integer data), so the id order of equal distances is exercised too."""
+    n = 4000
+    X, _ = synth.u8_mixture(n=n, d=d, components=6, seed=53 + d)
+    X = (X // 8).astype(np.uint8)  # coarse values: many equal distances
+    G = random_graph(n, 12, seed=54)
+    p = pc.params(k=6, R=12, L_search=12, L_dep=12, dep_threshold=0, max_dep_rounds=1, n_clusters=6)
+    r = run_pipeline(X, G, p)
+    P = oracle.Points(X)
+    o = oracle.knn_density(P, G, L=12, k=6)
+    assert (r["knn_ids"] == o["ids"]).all() and (r["rank_key"] == o["key"]).all()
+    d_ = oracle.dependent_points(P, G, o["key"], o["ids"], Ld=12, threshold=0, max_rounds=1)
+    assert d_["tail"] >= 100
+    assert (r["dep"] == d_["lam"]).all() and (r["dep_dist"] == d_["delta"]).all()
+    assert r["stats"][63] == d_["tail"]
+
+
 def test_edge_cases():
     # two points
     X = np.array([[0, 0, 0, 0], [3, 4, 0, 0]], np.float32)
