@@ -32,7 +32,7 @@ _lib = None
 F32, U8 = 0, 1
 L2, IP = 0, 1
 DENS_KTH, DENS_EXPSUM, DENS_SUMEXP, DENS_SUM = 0, 1, 2, 3
-CENTER_THRESHOLD, CENTER_PRODUCT = 0, 1
+CENTER_THRESHOLD, CENTER_PRODUCT, CENTER_LOCAL = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +71,8 @@ def _load():
         _lib.orc_dependent_points.restype = ctypes.c_int
         _lib.orc_cluster.argtypes = [i64, vp, vp, vp, i32, f32, f32, i32, vp]
         _lib.orc_cluster.restype = i64
+        _lib.orc_cluster_local.argtypes = [i64, i32, vp, vp, vp, vp, f32, vp]
+        _lib.orc_cluster_local.restype = i64
         _lib.orc_robust_prune.argtypes = [P, i64, vp, i64, f32, i32, vp]
         _lib.orc_robust_prune.restype = i32
         _lib.orc_build_graph.argtypes = [P, i32, i32, f32, vp, i32, f32, i32, i32, vp, ctypes.c_int]
@@ -181,16 +183,24 @@ def dependent_points(P: Points, G: np.ndarray, key: np.ndarray, knn_ids: np.ndar
 
 
 def cluster(rho, lam, delta, center: int = CENTER_PRODUCT, rho_min: float = 0.0,
-            delta_min: float = 0.0, n_clusters: int = 1):
+            delta_min: float = 0.0, n_clusters: int = 1, knn_ids=None, rank_key=None):
     """Noise, centers and union-find (Algorithm 2 lines 5-7). Returns
-    (labels, number_of_clusters); labels name each cluster by its root."""
+    (labels, number_of_clusters); labels name each cluster by its root.
+    The local center function (Appendix, center functions) also needs the
+    k-NN lists (n x k) and the rank keys."""
     rho = np.ascontiguousarray(rho, dtype=np.float32)
     lam = np.ascontiguousarray(lam, dtype=np.int32)
     delta = np.ascontiguousarray(delta, dtype=np.float32)
     n = rho.size
     labels = np.empty(n, np.int32)
-    nc = _load().orc_cluster(n, _p(rho), _p(lam), _p(delta), center, np.float32(rho_min),
-                             np.float32(delta_min), n_clusters, _p(labels))
+    if center == CENTER_LOCAL:
+        knn_ids = np.ascontiguousarray(knn_ids, dtype=np.int32).reshape(n, -1)
+        rank_key = np.ascontiguousarray(rank_key, dtype=np.float32)
+        nc = _load().orc_cluster_local(n, knn_ids.shape[1], _p(knn_ids), _p(rank_key), _p(rho), _p(lam),
+                                       np.float32(rho_min), _p(labels))
+    else:
+        nc = _load().orc_cluster(n, _p(rho), _p(lam), _p(delta), center, np.float32(rho_min),
+                                 np.float32(delta_min), n_clusters, _p(labels))
     if nc < 0:
         raise ValueError("orc_cluster: the dependent forest is inconsistent")
     return labels, int(nc)

@@ -15,6 +15,8 @@
  *   orc_dependent_points  Algorithm 3 (DPBruteForce + ComputeDepPts with the
  *                         doubling rounds and the brute-force tail of Sec. 3.2)
  *   orc_cluster           Algorithm 2 lines 5-7 (noise, center, union-find)
+ *   orc_cluster_local     the same with the local center function (Appendix,
+ *                         center functions)
  *   orc_robust_prune      RobustPrune(alpha, R) of Vamana (Sec. 3.2 defers it
  *                         to DiskANN; the published DiskANN rule is used)
  *   orc_build_graph       Vamana batched construction (Sec. 3.2, Sec. 4.1)
@@ -46,7 +48,7 @@
 enum { ORC_F32 = 0, ORC_U8 = 1 };
 enum { ORC_L2 = 0, ORC_IP = 1 };
 enum { DENS_KTH = 0, DENS_EXPSUM = 1, DENS_SUMEXP = 2, DENS_SUM = 3 };
-enum { CENTER_THRESHOLD = 0, CENTER_PRODUCT = 1 };
+enum { CENTER_THRESHOLD = 0, CENTER_PRODUCT = 1, CENTER_LOCAL = 2 };
 
 typedef struct {
   const void* X;  /* n x d row-major */
@@ -675,6 +677,44 @@ static int prod_cmp(const void* pa, const void* pb) {
   return a.id < b.id ? -1 : (a.id > b.id ? 1 : 0);
 }
 
+/* UF.Union(i, lambda_i) for every point that is neither noise nor a center
+ * nor without a dependent point; each set is named by its cut member. Frees
+ * noise and center. Returns the number of sets, or -1 on an inconsistent
+ * forest. */
+static int64_t cluster_from_centers(int64_t n, const int32_t* lam, uint8_t* noise, uint8_t* center,
+                                    int32_t* labels) {
+  int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  for (int64_t i = 0; i < n; i++) parent[i] = (int32_t)i;
+  /* UF.Union(i, lambda_i) for i not noise and not center */
+  for (int64_t i = 0; i < n; i++) {
+    if (noise[i] || center[i] || lam[i] < 0) continue;
+    int64_t a = uf_find(parent, i), b = uf_find(parent, lam[i]);
+    if (a != b) parent[a] = (int32_t)b;
+  }
+  /* name each set by its cut member */
+  int32_t* name = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  for (int64_t i = 0; i < n; i++) name[i] = -1;
+  int64_t roots = 0, bad = 0;
+  for (int64_t i = 0; i < n; i++) {
+    int cut = noise[i] || center[i] || lam[i] < 0;
+    if (!cut) continue;
+    int64_t r = uf_find(parent, i);
+    if (name[r] >= 0) bad = 1;
+    name[r] = (int32_t)i;
+    roots++;
+  }
+  for (int64_t i = 0; i < n; i++) {
+    int64_t r = uf_find(parent, i);
+    labels[i] = name[r];
+    if (name[r] < 0) bad = 1;
+  }
+  free(name);
+  free(parent);
+  free(noise);
+  free(center);
+  return bad ? -1 : roots;
+}
+
 /*
  * Noise: rho_i < rho_min (Sec. 4.2). Centers among the non-noise points:
  * threshold, delta_i > delta_min (Sec. 2.1, Sec. 4.2); or product, the
@@ -707,36 +747,32 @@ int64_t orc_cluster(int64_t n, const float* rho, const int32_t* lam, const float
     for (int64_t t = 0; t < m && t < n_clusters; t++) center[pr[t].id] = 1;
     free(pr);
   }
-  int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-  for (int64_t i = 0; i < n; i++) parent[i] = (int32_t)i;
-  /* UF.Union(i, lambda_i) for i not noise and not center */
+  return cluster_from_centers(n, lam, noise, center, labels);
+}
+
+/*
+ * Local center function (Appendix, center functions): a non-noise point is a
+ * center when it has the highest density among its k nearest neighbours, read
+ * as: it ranks above every listed neighbour j (rank_key_i > rank_key_j, or
+ * equal keys and i < j; entries < 0 are padding). Noise and union-find as in
+ * orc_cluster.
+ */
+int64_t orc_cluster_local(int64_t n, int32_t k, const int32_t* knn_ids, const float* rank_key,
+                          const float* rho, const int32_t* lam, float rho_min, int32_t* labels) {
+  uint8_t* noise = (uint8_t*)calloc((size_t)n, 1);
+  uint8_t* center = (uint8_t*)calloc((size_t)n, 1);
   for (int64_t i = 0; i < n; i++) {
-    if (noise[i] || center[i] || lam[i] < 0) continue;
-    int64_t a = uf_find(parent, i), b = uf_find(parent, lam[i]);
-    if (a != b) parent[a] = (int32_t)b;
+    noise[i] = rho[i] < rho_min;
+    if (noise[i]) continue;
+    int top = 1;
+    for (int32_t t = 0; t < k && top; t++) {
+      int32_t j = knn_ids[i * k + t];
+      if (j < 0 || j == i) continue;
+      if (rank_key[j] > rank_key[i] || (rank_key[j] == rank_key[i] && j < i)) top = 0;
+    }
+    center[i] = (uint8_t)top;
   }
-  /* name each set by its cut member */
-  int32_t* name = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-  for (int64_t i = 0; i < n; i++) name[i] = -1;
-  int64_t roots = 0, bad = 0;
-  for (int64_t i = 0; i < n; i++) {
-    int cut = noise[i] || center[i] || lam[i] < 0;
-    if (!cut) continue;
-    int64_t r = uf_find(parent, i);
-    if (name[r] >= 0) bad = 1;
-    name[r] = (int32_t)i;
-    roots++;
-  }
-  for (int64_t i = 0; i < n; i++) {
-    int64_t r = uf_find(parent, i);
-    labels[i] = name[r];
-    if (name[r] < 0) bad = 1;
-  }
-  free(name);
-  free(parent);
-  free(noise);
-  free(center);
-  return bad ? -1 : roots;
+  return cluster_from_centers(n, lam, noise, center, labels);
 }
 
 /* ---------- Vamana: RobustPrune and batched construction ---------- */

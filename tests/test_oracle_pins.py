@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from oracle import exact
+from paper_2312_03940_gb300 import synth
 from tests.helpers import example_arrays, random_graph, ranks_above
 
 
@@ -80,6 +81,59 @@ def test_example_clusters(golden_example):
         assert nc == 3
         # the label of a cluster is its root: b, d and the noise point e
         assert {names[l] for l in labels} == {"b", "d", "e"}
+
+
+def test_example_local_center(golden_example):
+    """Local center function (Appendix, center functions) on the Sec. 3
+    example, worked by hand from the printed k = 1 neighbours and densities:
+    b ranks above its neighbour c (equal density, smaller id) and d above f
+    (likewise); a, c, e and f rank below theirs. With rho_min = 1/sqrt(2) the
+    clusters are the printed ones, {a,b,c}, {d,f}, {e}; without a noise
+    threshold e follows its dependent point d."""
+    X, G, names, idx = example_arrays(golden_example)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=1, k=1)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=2, threshold=0)
+    rho_min = np.float32(1.0) / np.sqrt(np.float32(2.0))
+
+    def groups_of(labels):
+        g = {}
+        for i, l in enumerate(labels):
+            g.setdefault(int(l), []).append(names[i])
+        return sorted(sorted(v) for v in g.values())
+
+    labels, nc = oracle.cluster(r["rho"], dep["lam"], dep["delta"], center=oracle.CENTER_LOCAL,
+                                rho_min=rho_min, knn_ids=r["ids"], rank_key=r["key"])
+    assert groups_of(labels) == sorted(sorted(c) for c in golden_example["clusters"]) and nc == 3
+    assert {names[l] for l in labels} == {"b", "d", "e"}
+    labels, nc = oracle.cluster(r["rho"], dep["lam"], dep["delta"], center=oracle.CENTER_LOCAL,
+                                rho_min=0.0, knn_ids=r["ids"], rank_key=r["key"])
+    assert groups_of(labels) == [["a", "b", "c"], ["d", "e", "f"]] and nc == 2
+
+
+def test_local_center_forest_invariants():
+    """On a random mixture: every label is a root; the roots are exactly the
+    noise points, the points without a dependent point and the points ranked
+    above all their k nearest neighbours; every other point has its dependent
+    point's label."""
+    X, _ = synth.gaussian_mixture(n=1500, d=8, components=5, seed=71)
+    G = random_graph(1500, 12, seed=71)
+    P = oracle.Points(X)
+    r = oracle.knn_density(P, G, L=24, k=6)
+    dep = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=24, threshold=300)
+    rho_min = float(np.quantile(r["rho"], 0.05))
+    labels, nc = oracle.cluster(r["rho"], dep["lam"], dep["delta"], center=oracle.CENTER_LOCAL,
+                                rho_min=rho_min, knn_ids=r["ids"], rank_key=r["key"])
+    key, ids, lam = r["key"], r["ids"], dep["lam"]
+    n = len(labels)
+    top = np.array([all(not (key[j] > key[i] or (key[j] == key[i] and j < i)) for j in ids[i] if j >= 0 and j != i)
+                    for i in range(n)])
+    cut = (r["rho"] < np.float32(rho_min)) | (lam < 0) | top
+    assert (labels[labels] == labels).all()
+    assert set(np.flatnonzero(labels == np.arange(n))) == set(np.flatnonzero(cut))
+    assert nc == cut.sum()
+    inner = np.flatnonzero(~cut)
+    assert (labels[inner] == labels[lam[inner]]).all()
 
 
 # ---------------------------------------------------------------- distances
