@@ -91,10 +91,12 @@ typedef enum {
   PECANN_DENS_SUM = 3     /* rho = -sum_j D                               */
 } pecann_density_fn;
 
-/* Center functions (Sec. 4.2). */
+/* Center functions (Sec. 4.2; local: Appendix, center functions). */
 typedef enum {
   PECANN_CENTER_THRESHOLD = 0, /* delta_i > delta_min                   */
-  PECANN_CENTER_PRODUCT = 1    /* the n_clusters largest delta_i * rho_i  */
+  PECANN_CENTER_PRODUCT = 1,   /* the n_clusters largest delta_i * rho_i  */
+  PECANN_CENTER_LOCAL = 2      /* i ranks above each of its k neighbours
+                                  (pecann_cluster_sweep only)            */
 } pecann_center_fn;
 
 /* Parameters of the method. pecann_params_default() fills the paper's
@@ -256,6 +258,39 @@ PECANN_API pecann_status pecann_dependent_points(const pecann_dataset* ds, const
 PECANN_API pecann_status pecann_cluster(int64_t n, const float* d_density, const int32_t* d_dep,
                              const float* d_dep_dist, const pecann_params* p, int32_t* d_labels,
                              int64_t* h_n_clusters, void* ws, size_t ws_bytes, void* stream);
+
+/* One clustering of a sweep: center function and its parameters. */
+typedef struct {
+  int32_t center;     /* pecann_center_fn                                     */
+  float rho_min;      /* noise: rho_i < rho_min                               */
+  float delta_min;    /* threshold center                                     */
+  int32_t n_clusters; /* product center (>= 1)                                */
+} pecann_cluster_setting;
+
+/*
+ * Many clusterings from one dependent forest (Sec. 1: the dependent-point
+ * tree is a cluster hierarchy, and other clusterings come from re-running only
+ * the last step with other pruning settings; Appendix, varying number of
+ * clusters). For every setting s of the
+ * HOST array h_settings[0 .. n_settings), the rules of pecann_cluster apply
+ * and d_labels[s * n .. s * n + n) receives its labels. The local center
+ * (PECANN_CENTER_LOCAL) marks as centers the non-noise points that rank
+ * above each of their k nearest neighbours (the n x k d_knn_ids of
+ * pecann_density, -1 entries ignored; rank by d_rank_key, ties to the smaller
+ * id); d_knn_ids and d_rank_key may be NULL when no setting uses it.
+ * n_settings in 1..4096. If h_n_clusters (HOST, n_settings entries) is not
+ * NULL it receives each setting's number of clusters and the call waits for
+ * the stream. Workspace: pecann_cluster_workspace_size(n, n_settings).
+ * Errors: PECANN_EINVAL for a bad setting (unknown center function,
+ * n_clusters < 1 with the product center, a local center without k-NN lists)
+ * -- checked on the host before any GPU work.
+ */
+PECANN_API pecann_status pecann_cluster_workspace_size(int64_t n, int32_t n_settings, size_t* bytes);
+PECANN_API pecann_status pecann_cluster_sweep(int64_t n, const float* d_density, const int32_t* d_dep,
+                                   const float* d_dep_dist, const int32_t* d_knn_ids, int32_t k,
+                                   const float* d_rank_key, int32_t n_settings,
+                                   const pecann_cluster_setting* h_settings, int32_t* d_labels,
+                                   int64_t* h_n_clusters, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Batched form (many independent FP32 point sets of uneven sizes): the whole

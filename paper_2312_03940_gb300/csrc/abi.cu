@@ -7,6 +7,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -14,8 +15,9 @@
 namespace pecann {
 
 cudaError_t run_cluster(int64_t n, const float* rho, const int32_t* lam, const float* delta, int center_fn,
-                        float rho_min, float delta_min, int32_t n_clusters, int32_t* labels, void* ws,
-                        unsigned long long* d_roots, cudaStream_t st);
+                        float rho_min, float delta_min, int32_t n_clusters, const int32_t* knn_ids, int k,
+                        const float* rank_key, int32_t* labels, void* ws, unsigned long long* d_roots,
+                        cudaStream_t st);
 size_t cluster_ws_bytes(int64_t n);
 size_t build_ws_bytes(int64_t n, const pecann_params& p, int64_t cap, int vcap);
 int64_t batch_cap_of(int64_t n, float frac);
@@ -512,6 +514,8 @@ pecann_status pecann_cluster(int64_t n, const float* d_density, const int32_t* d
   if (!p || !d_density || !d_dep || !d_dep_dist || !d_labels || !ws)
     return set_last_error("NULL pointer"), PECANN_EINVAL;
   if (n < 1 || n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
+  if (p->center == PECANN_CENTER_LOCAL)
+    return set_last_error("the local center needs the k-NN lists: use pecann_cluster_sweep"), PECANN_EINVAL;
   if (p->center != PECANN_CENTER_THRESHOLD && p->center != PECANN_CENTER_PRODUCT)
     return set_last_error("bad center function"), PECANN_EINVAL;
   if (p->center == PECANN_CENTER_PRODUCT && p->n_clusters < 1)
@@ -520,7 +524,8 @@ pecann_status pecann_cluster(int64_t n, const float* d_density, const int32_t* d
   cudaStream_t st = (cudaStream_t)stream;
   WsHeader* h = (WsHeader*)ws;
   cudaError_t e = run_cluster(n, d_density, d_dep, d_dep_dist, p->center, p->rho_min, p->delta_min, p->n_clusters,
-                              d_labels, (uint8_t*)ws + HDR, h_n_clusters ? &h->roots : nullptr, st);
+                              nullptr, 0, nullptr, d_labels, (uint8_t*)ws + HDR,
+                              h_n_clusters ? &h->roots : nullptr, st);
   pecann_status s = cuda_status(e, "cluster");
   if (s) return s;
   if (h_n_clusters) {
@@ -529,6 +534,55 @@ pecann_status pecann_cluster(int64_t n, const float* d_density, const int32_t* d
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if ((s = cuda_status(e, "readback"))) return s;
     *h_n_clusters = (int64_t)r;
+  }
+  return PECANN_OK;
+}
+
+static size_t sweep_counts_offset(int64_t n) { return (HDR + cluster_ws_bytes(n) + 255) & ~(size_t)255; }
+
+pecann_status pecann_cluster_workspace_size(int64_t n, int32_t n_settings, size_t* bytes) {
+  if (!bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
+  if (n < 1 || n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
+  if (n_settings < 1 || n_settings > 4096) return set_last_error("n_settings must be in 1..4096"), PECANN_EINVAL;
+  *bytes = sweep_counts_offset(n) + (size_t)n_settings * 8;
+  return PECANN_OK;
+}
+
+pecann_status pecann_cluster_sweep(int64_t n, const float* d_density, const int32_t* d_dep, const float* d_dep_dist,
+                                   const int32_t* d_knn_ids, int32_t k, const float* d_rank_key, int32_t n_settings,
+                                   const pecann_cluster_setting* h_settings, int32_t* d_labels,
+                                   int64_t* h_n_clusters, void* ws, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  pecann_status s = pecann_cluster_workspace_size(n, n_settings, &need);
+  if (s) return s;
+  if (!d_density || !d_dep || !d_dep_dist || !h_settings || !d_labels || !ws)
+    return set_last_error("NULL pointer"), PECANN_EINVAL;
+  for (int32_t i = 0; i < n_settings; i++) {
+    const pecann_cluster_setting& c = h_settings[i];
+    if (c.center != PECANN_CENTER_THRESHOLD && c.center != PECANN_CENTER_PRODUCT && c.center != PECANN_CENTER_LOCAL)
+      return set_last_error("setting " + std::to_string(i) + ": bad center function"), PECANN_EINVAL;
+    if (c.center == PECANN_CENTER_PRODUCT && c.n_clusters < 1)
+      return set_last_error("setting " + std::to_string(i) + ": n_clusters must be >= 1"), PECANN_EINVAL;
+    if (c.center == PECANN_CENTER_LOCAL && (!d_knn_ids || !d_rank_key || k < 1))
+      return set_last_error("setting " + std::to_string(i) + ": the local center needs d_knn_ids, k >= 1 and "
+                            "d_rank_key"), PECANN_EINVAL;
+  }
+  if (ws_bytes < need) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* counts = (unsigned long long*)((uint8_t*)ws + sweep_counts_offset(n));
+  for (int32_t i = 0; i < n_settings; i++) {
+    const pecann_cluster_setting& c = h_settings[i];
+    cudaError_t e = run_cluster(n, d_density, d_dep, d_dep_dist, c.center, c.rho_min, c.delta_min, c.n_clusters,
+                                d_knn_ids, k, d_rank_key, d_labels + (int64_t)i * n, (uint8_t*)ws + HDR,
+                                h_n_clusters ? counts + i : nullptr, st);
+    if ((s = cuda_status(e, "cluster sweep"))) return s;
+  }
+  if (h_n_clusters) {
+    std::vector<unsigned long long> r((size_t)n_settings);
+    cudaError_t e = cudaMemcpyAsync(r.data(), counts, (size_t)n_settings * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if ((s = cuda_status(e, "readback"))) return s;
+    for (int32_t i = 0; i < n_settings; i++) h_n_clusters[i] = (int64_t)r[i];
   }
   return PECANN_OK;
 }

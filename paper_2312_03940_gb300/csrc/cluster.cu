@@ -106,13 +106,25 @@ __global__ void __launch_bounds__(1024) k_select_pick(SelectState* s, int pass, 
 
 __global__ void k_cluster_parent(int64_t n, const float* rho, const float* delta, const int32_t* lam,
                                  int center_fn, float rho_min, float delta_min,
-                                 const unsigned long long* keys, const SelectState* s, int32_t* parent) {
+                                 const unsigned long long* keys, const SelectState* s, const int32_t* knn_ids,
+                                 int k, const float* rk, int32_t* parent) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     bool noise = rho[i] < rho_min;
     bool center;
     if (center_fn == PECANN_CENTER_THRESHOLD) {
       center = !noise && delta[i] > delta_min;
+    } else if (center_fn == PECANN_CENTER_LOCAL) {
+      // ranks above each of its k nearest neighbours
+      center = !noise;
+      const float ki = rk[i];
+      for (int t = 0; t < k && center; t++) {
+        const int32_t j = knn_ids[i * k + t];
+        if (j >= 0 && j != (int32_t)i) {
+          const float kj = rk[j];
+          if (kj > ki || (kj == ki && j < (int32_t)i)) center = false;
+        }
+      }
     } else {
       unsigned long long kk = keys[i];
       center = kk != 0 && (s->all || kk >= s->prefix);
@@ -144,8 +156,9 @@ __global__ void k_count_roots(int64_t n, const int32_t* parent, unsigned long lo
 }
 
 cudaError_t run_cluster(int64_t n, const float* rho, const int32_t* lam, const float* delta, int center_fn,
-                        float rho_min, float delta_min, int32_t n_clusters, int32_t* labels, void* ws,
-                        unsigned long long* d_roots, cudaStream_t st) {
+                        float rho_min, float delta_min, int32_t n_clusters, const int32_t* knn_ids, int k,
+                        const float* rank_key, int32_t* labels, void* ws, unsigned long long* d_roots,
+                        cudaStream_t st) {
   // ws: keys n u64 | hist 65536 u32 | state | counters
   uint8_t* w = (uint8_t*)ws;
   unsigned long long* keys = (unsigned long long*)w;
@@ -169,7 +182,7 @@ cudaError_t run_cluster(int64_t n, const float* rho, const int32_t* lam, const f
     }
   }
   k_cluster_parent<<<blocks, threads, 0, st>>>(n, rho, delta, lam, center_fn, rho_min, delta_min, keys, s,
-                                               labels); note_launch();
+                                               knn_ids, k, rank_key, labels); note_launch();
   int sweeps = 1;
   while (((int64_t)1 << sweeps) < n) sweeps++;
   for (int it = 0; it <= sweeps; it++) {

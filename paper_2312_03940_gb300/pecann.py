@@ -19,7 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EINTERNAL = range(7)
 F32, U8, BF16, FP8E4M3 = 0, 1, 2, 3
 L2, IP = 0, 1
 DENS_KTH, DENS_EXPSUM, DENS_SUMEXP, DENS_SUM = 0, 1, 2, 3
-CENTER_THRESHOLD, CENTER_PRODUCT = 0, 1
+CENTER_THRESHOLD, CENTER_PRODUCT, CENTER_LOCAL = 0, 1, 2
 
 _DTYPES = {torch.float32: F32, torch.uint8: U8, torch.bfloat16: BF16}
 if hasattr(torch, "float8_e4m3fn"):
@@ -45,11 +45,16 @@ class PecannDataset(ctypes.Structure):
                 ("dim_scale", ctypes.c_void_p), ("data_f32", ctypes.c_void_p)]
 
 
+class PecannClusterSetting(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_int32), ("rho_min", ctypes.c_float), ("delta_min", ctypes.c_float),
+                ("n_clusters", ctypes.c_int32)]
+
+
 EXPORTS = ["pecann_params_default", "pecann_status_string", "pecann_last_error", "pecann_version",
            "pecann_kernel_launches",
            "pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
            "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
-           "pecann_batch_prepare", "pecann_run_batched"]
+           "pecann_batch_prepare", "pecann_run_batched", "pecann_cluster_workspace_size", "pecann_cluster_sweep"]
 
 NOALLOC_MAX_POINTS = 1 << 20
 
@@ -90,9 +95,12 @@ def load_library(path: str | None = None):
     lib.pecann_dependent_points.argtypes = [D, vp, P, vp, vp, vp, vp, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.pecann_cluster.argtypes = [i64, vp, vp, vp, P, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.pecann_density_noalloc.argtypes = [D, vp, P, vp, vp, vp, vp, vp]
+    lib.pecann_cluster_workspace_size.argtypes = [i64, i32, ctypes.POINTER(sz)]
+    lib.pecann_cluster_sweep.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, ctypes.POINTER(PecannClusterSetting),
+                                         vp, ctypes.POINTER(i64), vp, sz, vp]
     for f in ["pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
               "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
-           "pecann_batch_prepare", "pecann_run_batched"]:
+              "pecann_batch_prepare", "pecann_run_batched", "pecann_cluster_workspace_size", "pecann_cluster_sweep"]:
         getattr(lib, f).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -293,6 +301,40 @@ def pecann_cluster(density: torch.Tensor, dep: torch.Tensor, dep_dist: torch.Ten
                                          _ptr(labels), ctypes.byref(nc) if count else None, _ptr(ws),
                                          ws.numel(), _stream(stream)))
     return labels, (nc.value if count else None)
+
+
+def pecann_cluster_sweep(density: torch.Tensor, dep: torch.Tensor, dep_dist: torch.Tensor, settings,
+                         knn_ids: torch.Tensor | None = None, rank_key: torch.Tensor | None = None,
+                         ws: torch.Tensor | None = None, stream=None, count: bool = True):
+    """Many clusterings of one dependent forest. `settings`: a list of dicts with
+    keys center, rho_min, delta_min, n_clusters (missing keys: 0, 0, 0, 1).
+    The local center needs knn_ids (n, k) and rank_key. Returns (labels
+    (len(settings), n) int32, list of cluster counts or None)."""
+    _cuda(density, "density", torch.float32)
+    _cuda(dep, "dep", torch.int32)
+    _cuda(dep_dist, "dep_dist", torch.float32)
+    k = 0
+    if knn_ids is not None:
+        _cuda(knn_ids, "knn_ids", torch.int32)
+        k = knn_ids.shape[1]
+    if rank_key is not None:
+        _cuda(rank_key, "rank_key", torch.float32)
+    n, m = density.numel(), len(settings)
+    arr = (PecannClusterSetting * max(m, 1))()
+    for i, st in enumerate(settings):
+        arr[i] = PecannClusterSetting(int(st.get("center", CENTER_THRESHOLD)), float(st.get("rho_min", 0.0)),
+                                      float(st.get("delta_min", 0.0)), int(st.get("n_clusters", 1)))
+    lib = load_library()
+    if ws is None:
+        b = ctypes.c_size_t(0)
+        _check(lib.pecann_cluster_workspace_size(n, m, ctypes.byref(b)))
+        ws = torch.empty(b.value, dtype=torch.uint8, device=density.device)
+    labels = torch.empty((m, n), dtype=torch.int32, device=density.device)
+    counts = (ctypes.c_int64 * max(m, 1))()
+    _check(lib.pecann_cluster_sweep(n, _ptr(density), _ptr(dep), _ptr(dep_dist), _ptr(knn_ids), k, _ptr(rank_key),
+                                    m, arr, _ptr(labels), counts if count else None, _ptr(ws), ws.numel(),
+                                    _stream(stream)))
+    return labels, ([int(counts[i]) for i in range(m)] if count else None)
 
 
 class Batch:

@@ -47,6 +47,7 @@ def test_struct_layout_matches_header(lib):
     # pecann_params: 24 four-byte fields, then a uint64 -> 104 bytes
     assert ctypes.sizeof(pc.PecannParams) == 104
     assert ctypes.sizeof(pc.PecannDataset) == 48
+    assert ctypes.sizeof(pc.PecannClusterSetting) == 16
 
 
 def test_invalid_arguments_rejected_on_host(lib):
@@ -74,3 +75,24 @@ def test_workspace_size_is_host_only(lib):
     b = ctypes.c_size_t(0)
     assert lib.pecann_workspace_size(ctypes.byref(ds), ctypes.byref(p), ctypes.byref(b)) == pc.OK
     assert 16 * 1_000_000 < b.value < 1 << 31
+
+
+def test_cluster_sweep_checks_on_host(lib):
+    """Workspace sizing and every setting check answer on the host (the fake
+    device pointers below are never dereferenced)."""
+    b = ctypes.c_size_t(0)
+    assert lib.pecann_cluster_workspace_size(1000, 3, ctypes.byref(b)) == pc.OK and b.value >= 1000 * 8 + 3 * 8
+    assert lib.pecann_cluster_workspace_size(0, 3, ctypes.byref(b)) == pc.EINVAL
+    assert lib.pecann_cluster_workspace_size(1000, 0, ctypes.byref(b)) == pc.EINVAL
+    fake = ctypes.c_void_p(256)
+
+    def sweep(settings, knn=None, k=0, rk=None):
+        arr = (pc.PecannClusterSetting * len(settings))(*settings)
+        return lib.pecann_cluster_sweep(1000, fake, fake, fake, knn, k, rk, len(settings), arr, fake, None, fake,
+                                        1 << 30, None)
+
+    S = pc.PecannClusterSetting
+    assert sweep([S(7, 0.0, 0.0, 1)]) == pc.EINVAL                      # unknown center function
+    assert sweep([S(pc.CENTER_PRODUCT, 0.0, 0.0, 0)]) == pc.EINVAL      # n_clusters < 1
+    assert sweep([S(pc.CENTER_LOCAL, 0.0, 0.0, 1)]) == pc.EINVAL        # local center without k-NN lists
+    assert b"local center" in lib.pecann_last_error()

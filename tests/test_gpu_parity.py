@@ -70,6 +70,78 @@ def test_example_through_the_abi(golden_example):
         assert got == rnd["candidates"]
 
 
+
+def test_example_local_center_through_the_abi(golden_example):
+    """The local center on the Sec. 3 example through pecann_cluster_sweep:
+    centers b and d; with rho_min = 1/sqrt(2) the printed clusters, without
+    noise e follows d."""
+    X, G, names, idx = example_arrays(golden_example)
+    p = pc.params(k=1, R=G.shape[1], L_search=1, L_dep=2, dep_threshold=0)
+    ds = pc.Dataset(t(X))
+    ws = pc.workspace(ds, p)
+    dens = pc.pecann_density(ds, t(G), p, ws=ws)
+    dep = pc.pecann_dependent_points(ds, t(G), p, dens["rank_key"], dens["knn_ids"], dens["knn_dist"], ws=ws)
+    rho_min = float(np.float32(1) / np.sqrt(np.float32(2)))
+    labels, counts = pc.pecann_cluster_sweep(dens["density"], dep["dep"], dep["dep_dist"],
+                                             [dict(center=pc.CENTER_LOCAL, rho_min=rho_min),
+                                              dict(center=pc.CENTER_LOCAL, rho_min=0.0)],
+                                             knn_ids=dens["knn_ids"], rank_key=dens["rank_key"])
+    labels = labels.cpu().numpy()
+
+    def groups_of(lab):
+        g = {}
+        for i, l in enumerate(lab):
+            g.setdefault(int(l), []).append(names[i])
+        return sorted(sorted(v) for v in g.values())
+
+    assert groups_of(labels[0]) == sorted(sorted(c) for c in golden_example["clusters"]) and counts[0] == 3
+    assert groups_of(labels[1]) == [["a", "b", "c"], ["d", "e", "f"]] and counts[1] == 2
+
+
+def test_cluster_sweep_matches_single_calls_and_oracle():
+    """One dependent forest, nine clusterings (threshold, product and local
+    centers at three noise levels): each equals the oracle's clustering of the
+    oracle's own forest, and the single-setting call where it exists."""
+    n = 6000
+    X, _ = synth.gaussian_mixture(n=n, d=32, components=12, seed=81)
+    G = random_graph(n, 16, seed=81)
+    p = pc.params(k=8, R=16, L_search=32, L_dep=32, n_clusters=12)
+    ds = pc.Dataset(t(X))
+    ws = pc.workspace(ds, p)
+    dens = pc.pecann_density(ds, t(G), p, ws=ws)
+    dep = pc.pecann_dependent_points(ds, t(G), p, dens["rank_key"], dens["knn_ids"], dens["knn_dist"], ws=ws)
+    P = oracle.Points(X)
+    o = oracle.knn_density(P, G, L=32, k=8)
+    od = oracle.dependent_points(P, G, o["key"], o["ids"], Ld=32, threshold=300)
+    assert (dens["knn_ids"].cpu().numpy() == o["ids"]).all() and (dens["rank_key"].cpu().numpy() == o["key"]).all()
+    assert (dep["dep"].cpu().numpy() == od["lam"]).all() and (dep["dep_dist"].cpu().numpy() == od["delta"]).all()
+    qs = [float(v) for v in np.quantile(o["rho"], [0.0, 0.05, 0.25])]
+    dmin = float(np.median(od["delta"][np.isfinite(od["delta"])]))
+    settings = []
+    for rm in qs:
+        settings += [dict(center=pc.CENTER_THRESHOLD, rho_min=rm, delta_min=dmin),
+                     dict(center=pc.CENTER_PRODUCT, rho_min=rm, n_clusters=12),
+                     dict(center=pc.CENTER_LOCAL, rho_min=rm)]
+    labels, counts = pc.pecann_cluster_sweep(dens["density"], dep["dep"], dep["dep_dist"], settings,
+                                             knn_ids=dens["knn_ids"], rank_key=dens["rank_key"])
+    assert labels.shape == (len(settings), n)
+    for i, st in enumerate(settings):
+        ol, onc = oracle.cluster(o["rho"], od["lam"], od["delta"], center=st["center"], rho_min=st["rho_min"],
+                                 delta_min=st.get("delta_min", 0.0), n_clusters=st.get("n_clusters", 1),
+                                 knn_ids=o["ids"], rank_key=o["key"])
+        assert (labels[i].cpu().numpy() == ol).all(), st
+        assert counts[i] == onc, st
+        if st["center"] != pc.CENTER_LOCAL:
+            p1 = pc.params(center=st["center"], rho_min=st["rho_min"], delta_min=st.get("delta_min", 0.0),
+                           n_clusters=st.get("n_clusters", 1))
+            l1, n1 = pc.pecann_cluster(dens["density"], dep["dep"], dep["dep_dist"], p1)
+            assert torch.equal(l1, labels[i]) and n1 == counts[i]
+    # the local center needs the k-NN lists in the single-setting call
+    with pytest.raises(pc.PecannError) as e:
+        pc.pecann_cluster(dens["density"], dep["dep"], dep["dep_dist"], pc.params(center=pc.CENTER_LOCAL))
+    assert e.value.status == pc.EINVAL
+
+
 # ---------------------------------------------------------------- Algorithm 1
 
 @pytest.mark.parametrize("dtype,d,metric", [("f32", 32, pc.L2), ("f32", 128, pc.L2), ("u8", 128, pc.L2),
