@@ -203,6 +203,38 @@ def ari(a: np.ndarray, b: np.ndarray) -> float:
     return float((sum_ij - expected) / (max_index - expected))
 
 
+def homogeneity_completeness(pred: np.ndarray, true: np.ndarray) -> tuple:
+    """Homogeneity 1 - H(T|C) / H(T) and completeness 1 - H(C|T) / H(C) of
+    predicted clusters C against ground-truth classes T (Sec. 5 metrics).
+    The printed symbols swap C and T against the prose that defines them; the
+    prose and its example (every point its own cluster: homogeneity 1, low
+    completeness) are followed. Natural logarithms; a zero entropy in a
+    denominator gives 1."""
+    pred = np.asarray(pred).reshape(-1)
+    true = np.asarray(true).reshape(-1)
+    n = pred.size
+    _, ci = np.unique(pred, return_inverse=True)
+    _, ti = np.unique(true, return_inverse=True)
+    cont = np.zeros((ti.max() + 1, ci.max() + 1), np.int64)
+    np.add.at(cont, (ti, ci), 1)
+    a = cont.sum(1).astype(np.float64)  # class sizes
+    b = cont.sum(0).astype(np.float64)  # cluster sizes
+    nz = cont > 0
+    nij = cont[nz].astype(np.float64)
+    ii, jj = np.nonzero(nz)
+
+    def entropy(sizes):
+        q = sizes[sizes > 0] / n
+        return float(-(q * np.log(q)).sum())
+
+    h_t, h_c = entropy(a), entropy(b)
+    h_t_given_c = float(-((nij / n) * np.log(nij / b[jj])).sum())
+    h_c_given_t = float(-((nij / n) * np.log(nij / a[ii])).sum())
+    hom = 1.0 if h_t == 0.0 else 1.0 - h_t_given_c / h_t
+    com = 1.0 if h_c == 0.0 else 1.0 - h_c_given_t / h_c
+    return hom, com
+
+
 def knn_recall(found_dist: np.ndarray, exact_dist: np.ndarray, rel: float = 1e-5) -> float:
     """Tie-aware recall: per query, the fraction of the k returned points whose
     distance is within (1 + rel) of the exact k-th distance; averaged."""

@@ -136,6 +136,28 @@ def test_local_center_forest_invariants():
     assert (labels[inner] == labels[lam[inner]]).all()
 
 
+def test_homogeneity_completeness_closed_forms():
+    """Sec. 6 metrics: identical partitions give (1, 1); every point its own
+    cluster against K equal classes gives homogeneity 1 and completeness
+    1 - log(n/K) / log(n) (the paper's example of a low completeness); one
+    cluster for everything gives (0, 1); scikit-learn agrees when installed."""
+    true = np.repeat(np.arange(10), 100)
+    assert exact.homogeneity_completeness(true, true) == pytest.approx((1.0, 1.0))
+    hom, com = exact.homogeneity_completeness(np.arange(1000), true)
+    assert hom == pytest.approx(1.0) and com == pytest.approx(1.0 - np.log(100) / np.log(1000))
+    assert com == pytest.approx(1.0 / 3.0)
+    assert exact.homogeneity_completeness(np.zeros(1000), true) == pytest.approx((0.0, 1.0))
+    g = np.random.default_rng(3)
+    pred = g.integers(0, 7, size=1000)
+    try:
+        from sklearn.metrics import completeness_score, homogeneity_score
+    except ImportError:
+        return
+    hom, com = exact.homogeneity_completeness(pred, true)
+    assert hom == pytest.approx(homogeneity_score(true, pred), abs=1e-12)
+    assert com == pytest.approx(completeness_score(true, pred), abs=1e-12)
+
+
 # ---------------------------------------------------------------- distances
 
 def test_canonical_distance_within_fp32_error_bound():
