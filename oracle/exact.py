@@ -205,7 +205,7 @@ def ari(a: np.ndarray, b: np.ndarray) -> float:
 
 def homogeneity_completeness(pred: np.ndarray, true: np.ndarray) -> tuple:
     """Homogeneity 1 - H(T|C) / H(T) and completeness 1 - H(C|T) / H(C) of
-    predicted clusters C against ground-truth classes T (Sec. 5 metrics).
+    predicted clusters C against ground-truth classes T (Sec. 6 metrics).
     The printed symbols swap C and T against the prose that defines them; the
     prose and its example (every point its own cluster: homogeneity 1, low
     completeness) are followed. Natural logarithms; a zero entropy in a
