@@ -752,9 +752,9 @@ int64_t orc_cluster(int64_t n, const float* rho, const int32_t* lam, const float
 
 /*
  * Local center function (Appendix, center functions): a non-noise point is a
- * center when it has the highest density among its k nearest neighbours, read
- * as: it ranks above every listed neighbour j (rank_key_i > rank_key_j, or
- * equal keys and i < j; entries < 0 are padding). Noise and union-find as in
+ * center when no point of its k-NN list is denser, in the rank order above:
+ * it ranks above every listed neighbour j (rank_key_i > rank_key_j, or equal
+ * keys and i < j; entries < 0 are padding). Noise and union-find as in
  * orc_cluster.
  */
 int64_t orc_cluster_local(int64_t n, int32_t k, const int32_t* knn_ids, const float* rank_key,
