@@ -27,7 +27,9 @@
  *    CUDA call failed (the message is available from pecann_last_error());
  *    PECANN_EUNSUPPORTED: a valid combination this build has no kernel for;
  *    PECANN_EINTERNAL: a kernel detected an inconsistency (e.g. a graph entry
- *    out of range) and skipped the offending access.
+ *    out of range) and skipped the offending access. PECANN_ETIMEOUT is
+ *    reserved: no kernel of this library waits on another (the batched
+ *    form's work queue is a fetch-and-add counter), so no call returns it.
  *  - Point rows are n x d, row-major, contiguous, 16-byte aligned. d must be
  *    a multiple of 4 (FP32), 8 (BF16) or 16 (U8, FP8). U8 supports the L2
  *    metric with d <= 256 (so that every distance is an exact integer in FP32).

@@ -96,3 +96,20 @@ def test_cluster_sweep_checks_on_host(lib):
     assert sweep([S(pc.CENTER_PRODUCT, 0.0, 0.0, 0)]) == pc.EINVAL      # n_clusters < 1
     assert sweep([S(pc.CENTER_LOCAL, 0.0, 0.0, 1)]) == pc.EINVAL        # local center without k-NN lists
     assert b"local center" in lib.pecann_last_error()
+
+
+def test_small_workspace_is_enomem_on_host(lib):
+    """A workspace below what the call needs is PECANN_ENOMEM, answered on the
+    host before any GPU work (this machine has no GPU: a CUDA call would turn
+    the status into ECUDA)."""
+    p = pc.params(k=4, R=8, L_search=8, L_dep=8, n_clusters=2)
+    ds = pc.PecannDataset(256, 1000, 32, pc.F32, pc.L2, 0, None, None)
+    g = ctypes.c_void_p(256)
+    assert lib.pecann_density(ctypes.byref(ds), g, ctypes.byref(p), g, g, g, g, g, 64, None) == pc.ENOMEM
+    assert lib.pecann_dependent_points(ctypes.byref(ds), g, ctypes.byref(p), g, g, g, g, g, None, g, 64,
+                                       None) == pc.ENOMEM
+    assert lib.pecann_cluster(1000, g, g, g, ctypes.byref(p), g, None, g, 64, None) == pc.ENOMEM
+    S = pc.PecannClusterSetting
+    arr = (S * 1)(S(pc.CENTER_THRESHOLD, 0.0, 1.0, 1))
+    assert lib.pecann_cluster_sweep(1000, g, g, g, None, 0, None, 1, arr, g, None, g, 64, None) == pc.ENOMEM
+    assert b"workspace too small" in lib.pecann_last_error()
