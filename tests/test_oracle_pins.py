@@ -39,6 +39,36 @@ def test_example_density_and_rank(golden_example):
     assert [names[i] for i in order] == golden_example["rank_high_to_low"]
 
 
+def test_density_functions_closed_forms():
+    """Sec. 4.2 / Appendix A densities on a configuration worked out by hand:
+    a center c = (0, 0) and four vertices (+-2, 0), (0, +-2), complete graph,
+    k = 4 (so every k-NN list holds the other four points, exactly). For c all
+    four distances are 2; for a vertex they are 2, sqrt(8), sqrt(8) and 4.
+    kth: 1/2 and 1/4. exp-sum: exp(-16/4) and exp(-36/4). sum-exp: e^-4 and
+    (e^-4 + 2 e^-8 + e^-16) / 4. sum: -8 and -(6 + 4 sqrt 2). Normalised kth:
+    c: (1/2)(4) / (4 / 4) = 2; a vertex: (1/4)(4) / (1/2 + 3/4) = 0.8."""
+    X = np.zeros((5, 4), np.float32)  # two zero coordinates pad the rows to d = 4
+    X[:, :2] = [[0, 0], [2, 0], [-2, 0], [0, 2], [0, -2]]
+    G = np.array([[j for j in range(5) if j != i] for i in range(5)], np.int32)
+    P = oracle.Points(X)
+    e = np.exp
+    cases = [
+        (oracle.DENS_KTH, False, [0.5, 0.25], [0.5, 0.25]),
+        (oracle.DENS_EXPSUM, False, [e(-4.0), e(-9.0)], [-4.0, -9.0]),
+        (oracle.DENS_SUMEXP, False, [e(-4.0), (e(-4.0) + 2 * e(-8.0) + e(-16.0)) / 4],
+         [e(-4.0), (e(-4.0) + 2 * e(-8.0) + e(-16.0)) / 4]),
+        (oracle.DENS_SUM, False, [-8.0, -(6 + 4 * np.sqrt(2.0))], [-8.0, -(6 + 4 * np.sqrt(2.0))]),
+        (oracle.DENS_KTH, True, [2.0, 0.8], [2.0, 0.8]),
+    ]
+    for fn, norm, rho, key in cases:
+        r = oracle.knn_density(P, G, L=4, k=4, density=fn, normalize=norm)
+        assert (r["fallback"] == 0).all()
+        want_rho = np.array([rho[0]] + [rho[1]] * 4)
+        want_key = np.array([key[0]] + [key[1]] * 4)
+        assert np.allclose(r["rho"], want_rho, rtol=2e-6, atol=0), (fn, norm, r["rho"])
+        assert np.allclose(r["key"], want_key, rtol=2e-6, atol=0), (fn, norm, r["key"])
+
+
 def test_example_dependent_points_and_rounds(golden_example):
     """Fig. 2 dependent points and the Sec. 3.1 rounds for d (L_d = 2, threshold 0)."""
     X, G, names, idx = example_arrays(golden_example)
