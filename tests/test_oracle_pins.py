@@ -69,6 +69,23 @@ def test_density_functions_closed_forms():
         assert np.allclose(r["key"], want_key, rtol=2e-6, atol=0), (fn, norm, r["key"])
 
 
+def test_search_counts_by_hand_and_full_beam(golden_example):
+    """The per-query counts behind the algorithmic bytes: E_q (expansions, the
+    query's own out-list included) and C_q (distinct points scored). On the
+    Sec. 3 example with L = 1, counted by hand from the Fig. 1 graph: a
+    expands a, b, c and scores b, c, f (E 3, C 3); d expands d, f and scores
+    f, e, c (E 2, C 3); e expands e, d and scores d, f (E 2, C 2). With L >= n
+    on a connected graph every point is expanded once and every other point
+    scored once: E = n, C = n - 1."""
+    X, G, names, idx = example_arrays(golden_example)
+    e, c = oracle.search_counts(oracle.Points(X), G, [idx["a"], idx["d"], idx["e"]], L=1)
+    assert list(e) == [3, 2, 2] and list(c) == [3, 3, 2]
+    n = 300
+    X2, _ = synth.gaussian_mixture(n=n, d=8, components=3, seed=5)
+    e2, c2 = oracle.search_counts(oracle.Points(X2), random_graph(n, 6, seed=5), np.arange(0, n, 37), L=n)
+    assert (e2 == n).all() and (c2 == n - 1).all()
+
+
 def test_example_dependent_points_and_rounds(golden_example):
     """Fig. 2 dependent points and the Sec. 3.1 rounds for d (L_d = 2, threshold 0)."""
     X, G, names, idx = example_arrays(golden_example)
