@@ -528,3 +528,24 @@ def test_exact_oracle_against_python_loops():
             assert lam[i] == min(higher)[1]
         else:
             assert lam[i] == -1
+
+
+def test_exact_knn_queries_and_recall():
+    """exact_knn_queries (sampled rows, used at full size) equals exact_knn on
+    the same rows for both metrics. knn_recall closed forms: identical lists
+    give 1; two of four beyond the exact k-th distance give 0.5; a distance
+    within 1e-5 relative of the k-th counts (ties), one at 5e-5 does not."""
+    g = np.random.default_rng(22)
+    X = g.standard_normal((400, 16)).astype(np.float32)
+    Xn = (X / np.linalg.norm(X, axis=1, keepdims=True)).astype(np.float32)
+    rows = np.array([0, 7, 123, 399])
+    for Xm, metric in ((X, exact.L2), (Xn, exact.IP)):
+        ids, dist = exact.exact_knn(Xm, 5, metric=metric)
+        qi, qd = exact.exact_knn_queries(Xm, rows, 5, metric=metric)
+        assert (qi == ids[rows]).all()
+        assert np.allclose(qd, dist[rows], rtol=1e-12, atol=1e-15)
+    ex = np.array([[1.0, 2.0, 3.0, 4.0]])
+    assert exact.knn_recall(ex, ex) == 1.0
+    assert exact.knn_recall(np.array([[1.0, 2.0, 5.0, 6.0]]), ex) == 0.5
+    assert exact.knn_recall(np.array([[1.0, 2.0, 3.0, 4.0 * (1 + 5e-6)]]), ex) == 1.0
+    assert exact.knn_recall(np.array([[1.0, 2.0, 3.0, 4.0 * (1 + 5e-5)]]), ex) == 0.75
