@@ -33,6 +33,9 @@
  *  - Point rows are n x d, row-major, contiguous, 16-byte aligned. d must be
  *    a multiple of 4 (FP32), 8 (BF16) or 16 (U8, FP8). U8 supports the L2
  *    metric with d <= 256 (so that every distance is an exact integer in FP32).
+ *    Speed only: U8 rows of 128 bytes on a 32-byte aligned base (as torch
+ *    allocates) are scored with one 32-byte load per lane; other bases take
+ *    a 16-byte layout with the same results.
  *  - Reduced-precision traversal: a BF16 or FP8 dataset must also give
  *    data_f32, the same points in FP32. Graph searches walk the BF16 / FP8
  *    rows (FP32 accumulation); every distance that leaves the library (k-NN lists,
