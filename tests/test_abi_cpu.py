@@ -113,3 +113,22 @@ def test_small_workspace_is_enomem_on_host(lib):
     arr = (S * 1)(S(pc.CENTER_THRESHOLD, 0.0, 1.0, 1))
     assert lib.pecann_cluster_sweep(1000, g, g, g, None, 0, None, 1, arr, g, None, g, 64, None) == pc.ENOMEM
     assert b"workspace too small" in lib.pecann_last_error()
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """tests/c_abi_example.c includes include/pecann.h as C99 (-Wall -Werror),
+    links the shared library and calls host-only entry points."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(pbuild.LIB)
+    exe = str(tmp_path / "c_abi_example")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi_example.c"), "-L", libdir, "-lpecann",
+                        "-Wl,-rpath," + libdir, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "workspace ok" in r.stdout and "bad center function" in r.stdout
