@@ -178,29 +178,40 @@ def exact_dpc(X: np.ndarray, k: int, metric: int = L2, density_fn: str = "kth", 
 
 
 def ari(a: np.ndarray, b: np.ndarray) -> float:
-    """Adjusted Rand Index (Hubert and Arabie), with int64 pair counts.
-    Two identical partitions give 1.0, including the degenerate 0/0 case."""
+    """Adjusted Rand Index (Hubert and Arabie; the printed formula of Sec. 6.1
+    lacks a product sign, the standard definition is used).
+
+    With n_ij the contingency counts, a_i and b_j its row and column sums and
+    T = C(n, 2) the number of pairs:
+        ARI = (sum_ij C(n_ij, 2) - E) / ((S_a + S_b) / 2 - E),  E = S_a S_b / T,
+    S_a = sum_i C(a_i, 2), S_b = sum_j C(b_j, 2). Multiplying through by 2T
+    gives the integer ratio (2 T S_ij - 2 S_a S_b) / (T (S_a + S_b) - 2 S_a S_b),
+    evaluated here in Python integers (exact at any n: the products pass 2^63
+    near n = 10^5) and divided once in floating point. Two identical
+    partitions give 1.0, including the degenerate 0/0 case."""
     a = np.asarray(a).reshape(-1)
     b = np.asarray(b).reshape(-1)
-    n = a.size
+    n = int(a.size)
     _, ai = np.unique(a, return_inverse=True)
     _, bi = np.unique(b, return_inverse=True)
-    cont = np.zeros((ai.max() + 1, bi.max() + 1), np.int64)
-    np.add.at(cont, (ai, bi), 1)
+    # sparse contingency table: one entry per occupied (cluster, class) cell
+    cell = ai.astype(np.int64) * (int(bi.max()) + 1) + bi.astype(np.int64)
+    _, cont = np.unique(cell, return_counts=True)
 
-    def c2(x):
-        x = np.asarray(x, np.int64)
-        return (x * (x - 1) // 2).sum()
+    def c2(counts) -> int:
+        # each term x (x - 1) / 2 < 2^62 for x < 2^31; the sum in Python ints
+        x = np.asarray(counts, np.int64)
+        return sum(int(v) for v in (x * (x - 1) // 2))
 
-    sum_ij = c2(cont)
-    sum_a = c2(cont.sum(1))
-    sum_b = c2(cont.sum(0))
+    s_ij = c2(cont)
+    s_a = c2(np.bincount(ai))
+    s_b = c2(np.bincount(bi))
     total = n * (n - 1) // 2
-    expected = sum_a * sum_b / total if total else 0.0
-    max_index = 0.5 * (sum_a + sum_b)
-    if max_index == expected:
+    num = 2 * total * s_ij - 2 * s_a * s_b
+    den = total * (s_a + s_b) - 2 * s_a * s_b
+    if den == 0:
         return 1.0
-    return float((sum_ij - expected) / (max_index - expected))
+    return num / den  # correctly rounded quotient of two Python integers
 
 
 def homogeneity_completeness(pred: np.ndarray, true: np.ndarray) -> tuple:

@@ -378,6 +378,36 @@ def test_ari_matches_sklearn():
         assert abs(exact.ari(a, b) - sk.adjusted_rand_score(a, b)) < 1e-12
 
 
+def test_ari_closed_form_at_scale():
+    """Halves against quarters nested in them, n = 4m points. By hand: S_ij =
+    S_b = 2m(m-1), S_a = 2m(2m-1), T = 2m(4m-1); E = S_a S_b / T =
+    2m(2m-1)(m-1)/(4m-1) and (S_a + S_b)/2 = m(3m-2), so
+    ARI = 4m^2(m-1) / (m^2(8m-5)) = 4(m-1)/(8m-5). At n = 2,000,000 the
+    product S_a S_b is ~5e23, far beyond int64 (a 64-bit product would wrap)."""
+    for m in (1, 2, 3, 1000, 500_000, 1_250_000):
+        n = 4 * m
+        halves = np.arange(n) // (2 * m)
+        quarters = np.arange(n) // m
+        want = 4 * (m - 1) / (8 * m - 5)
+        assert abs(exact.ari(halves, quarters) - want) <= 1e-15, m
+        assert abs(exact.ari(quarters, halves) - want) <= 1e-15, m
+    # one label against n singletons: S_ij = S_b = 0, E = 0 -> ARI = 0
+    assert exact.ari(np.zeros(2_000_000, np.int64), np.arange(2_000_000)) == 0.0
+
+
+def test_ari_matches_sklearn_at_one_million():
+    """Random labels at n = 1,000,000 (pair counts ~1e11, their products ~1e22):
+    scikit-learn's ARI (which promotes to Python integers) agrees."""
+    sk = pytest.importorskip("sklearn.metrics")
+    g = np.random.default_rng(10)
+    n = 1_000_000
+    a = g.integers(0, 5, size=n)
+    b = np.where(g.random(n) < 0.8, a, g.integers(0, 7, size=n))
+    assert abs(exact.ari(a, b) - sk.adjusted_rand_score(a, b)) < 1e-12
+    c = g.integers(0, 1000, size=n)
+    assert abs(exact.ari(a, c) - sk.adjusted_rand_score(a, c)) < 1e-12
+
+
 def test_cluster_root_invariants():
     """Every label is the root of its tree: a point whose dependent edge was
     cut, labelled with itself; each non-root point shares its dependent point's label."""
