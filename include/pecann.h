@@ -17,10 +17,11 @@
  *    aligned, of at least pecann_workspace_size() bytes. Its contents on entry
  *    do not matter; on return they are undefined.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
- *    queued on it. pecann_search, pecann_build_graph and
- *    pecann_dependent_points return only after their work on `stream` has
- *    finished (they read back an error word or small counters); the other
- *    calls are asynchronous unless a host output is requested.
+ *    queued on it. pecann_search, pecann_build_graph, pecann_density,
+ *    pecann_density_noalloc and pecann_dependent_points return only after
+ *    their work on `stream` has finished (they read back an error word or
+ *    small counters); the other calls are asynchronous unless a host output
+ *    is requested.
  *  - Errors are returned as pecann_status; nothing is thrown across the ABI.
  *    PECANN_EINVAL: an argument is out of range (checked on the host before
  *    any GPU work); PECANN_ENOMEM: ws_bytes is too small; PECANN_ECUDA: a
@@ -222,6 +223,9 @@ PECANN_API pecann_status pecann_build_graph(const pecann_dataset* ds, const peca
  * the value points are ranked by -- rho, or the exponent -sum(D^2)/k for the
  * exp-sum density. Point j ranks above i iff key_j > key_i, or the keys are
  * equal and j < i (Sec. 3: ties broken by id).
+ * Blocks until done: the call ends by reading the kernels' error word, and
+ * returns PECANN_EINTERNAL when a search met a graph entry >= n (the entry
+ * is skipped, never read through; the outputs are then unspecified).
  */
 PECANN_API pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph,
                              const pecann_params* p, int32_t* d_knn_ids, float* d_knn_dist,
@@ -336,21 +340,23 @@ PECANN_API pecann_status pecann_run_batched(int32_t n_sets, const pecann_dataset
 
 /*
  * pecann_density without a workspace, for callers that cannot allocate GPU
- * memory (for example code running under an external memory manager that
- * owns every device byte, or a loop that must never take the allocator's
- * lock). The paper has no counterpart: this is a packaging of
- * pecann_density, with the same arguments minus the workspace and the same
- * results, element for element.
+ * memory (for example code under an external memory manager that owns every
+ * device byte, or a loop that must never take the allocator's lock, since a
+ * cudaMalloc can synchronise the device). The paper has no counterpart: this
+ * is a packaging of pecann_density, with the same arguments minus the
+ * workspace, the same checks and the same results, element for element.
  * Its scratch (about 8 MiB: a fallback list and a density copy for up to
  * PECANN_NOALLOC_MAX_POINTS points) is one fixed device array inside the
  * library, present on every GPU that loads the library until the process
  * exits. The call allocates nothing; n > PECANN_NOALLOC_MAX_POINTS returns
- * PECANN_EINVAL. The first call on each device looks the array's device
- * address up (cudaGetSymbolAddress); make that first call before any stream
- * capture. All calls share the array: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller. Each
- * call clears what must start at zero; the rest keeps the previous call's
- * contents. Asynchronous on `stream`, like pecann_density.
+ * PECANN_EINVAL, BF16 / FP8 rows PECANN_EUNSUPPORTED. Every call looks the
+ * array's device address up in the current context (cudaGetSymbolAddress);
+ * the first call on a device may load the library's device code there, so
+ * make it before any stream capture. All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. Each call clears what must start at zero; the
+ * rest keeps the previous call's contents. Like pecann_density it blocks
+ * until done and returns PECANN_EINTERNAL for a graph entry >= n.
  */
 PECANN_API pecann_status pecann_density_noalloc(const pecann_dataset* ds, const int32_t* d_graph,
                                                 const pecann_params* p, int32_t* d_knn_ids,

@@ -75,7 +75,7 @@ static bool is_reduced(int dtype) { return dtype == DT_BF16 || dtype == DT_FP8; 
 
 // Checks the dataset and fills the view of its rows; f32 (optional) gets the
 // FP32 rows: the same view for FP32 / U8 data, data_f32 for BF16 / FP8.
-static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataView* f32 = nullptr) {
+pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataView* f32) {
   if (!ds || !ds->data) return set_last_error("dataset or data pointer is NULL"), PECANN_EINVAL;
   if (ds->n < 2 || ds->n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
   if (ds->dtype < 0 || ds->dtype > 3 || ds->metric < 0 || ds->metric > 1)
@@ -119,12 +119,12 @@ static pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataV
 
 static const int DEP_RERANK = 32;  // dependent rounds: candidates re-scored per query
 
-static int rerank_k_of(const pecann_params* p) {
+int rerank_k_of(const pecann_params* p) {
   int K = p->rerank_k > 0 ? p->rerank_k : std::min(p->L_search, 4 * p->k);
   return std::max(K, p->k);
 }
 
-static int log2_hash(const pecann_params* p, int Lw) {
+int log2_hash(const pecann_params* p, int Lw) {
   int slots = p->hash_slots;
   if (slots <= 0) {
     // 8 slots per beam entry: at a beam of 128 this keeps a warp's shared
@@ -138,7 +138,7 @@ static int log2_hash(const pecann_params* p, int Lw) {
   return std::max(4, std::min(l, 16));
 }
 
-static pecann_status cuda_status(cudaError_t e, const char* what) {
+pecann_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return PECANN_OK;
   if (e == cudaErrorNotSupported) {
     set_last_error(std::string(what) + ": unsupported combination");
@@ -149,7 +149,7 @@ static pecann_status cuda_status(cudaError_t e, const char* what) {
   return PECANN_ECUDA;
 }
 
-static pecann_status read_err(int* d_err, cudaStream_t st) {
+pecann_status read_err(int* d_err, cudaStream_t st) {
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -162,7 +162,7 @@ static pecann_status read_err(int* d_err, cudaStream_t st) {
   return PECANN_OK;
 }
 
-static pecann_status check_params(const pecann_params* p, int64_t n) {
+pecann_status check_params(const pecann_params* p, int64_t n) {
   if (!p) return set_last_error("params is NULL"), PECANN_EINVAL;
   if (p->R < 1 || p->R > 256) return set_last_error("R must be in 1..256"), PECANN_EINVAL;
   if (p->k < 1 || p->k >= n || p->k > 1024) return set_last_error("k must be in 1..min(n-1, 1024)"), PECANN_EINVAL;
@@ -182,6 +182,88 @@ static size_t dep_bytes(int64_t n, bool reduced) {
   size_t b = 2 * al((size_t)n * 4) + al((size_t)n * 8);
   if (reduced) b += al((size_t)n * DEP_RERANK * 4) + al((size_t)n * 4);
   return b;
+}
+
+pecann_status check_density_args(const DataView& dv, const int32_t* d_graph, const pecann_params* p,
+                                 const int32_t* d_knn_ids, const float* d_knn_dist, const float* d_density,
+                                 const float* d_rank_key) {
+  pecann_status s = check_params(p, dv.n);
+  if (s) return s;
+  if (!d_graph || !d_knn_ids || !d_knn_dist || !d_density || !d_rank_key)
+    return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if (p->density < 0 || p->density > 3) return set_last_error("bad density function"), PECANN_EINVAL;
+  if (is_reduced(dv.dtype) && rerank_k_of(p) > p->L_search)
+    return set_last_error("rerank_k must be in k..L_search"), PECANN_EINVAL;
+  return PECANN_OK;
+}
+
+// k-NN + density (Algorithm 2 lines 2-4) on checked arguments: the beam
+// search over every point, the FP32 re-rank for reduced-precision rows, the
+// brute-force k-NN of the points whose search returned fewer than k, the
+// optional normalisation; then the error word is read back, so that a kernel
+// that met an out-of-range graph id makes the call return PECANN_EINTERNAL.
+// *sc.err and *sc.fb_cnt must be zero on entry.
+pecann_status run_density(const DataView& dv, const DataView& fv, const int32_t* d_graph, const pecann_params* p,
+                          int32_t* d_knn_ids, float* d_knn_dist, float* d_density, float* d_rank_key,
+                          const DensityScratch& sc, cudaStream_t st) {
+  const bool reduced = is_reduced(dv.dtype);
+  const int K = reduced ? rerank_k_of(p) : 0;
+  if (reduced && !sc.rr_ids) return set_last_error("no re-rank scratch for BF16 / FP8 rows"), PECANN_EUNSUPPORTED;
+  pecann_status s;
+  cudaError_t e;
+  SearchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.X = dv.X;
+  a.row_bytes = dv.row_bytes;
+  a.n = dv.n;
+  a.C = dv.C;
+  a.G = d_graph;
+  a.R = p->R;
+  a.queries = nullptr;
+  a.nq = dv.n;
+  a.Lw = p->L_search;
+  a.log2h = log2_hash(p, a.Lw);
+  a.stage = (p->R + 31) & ~31;
+  a.mode = MODE_KNN;
+  a.metric = dv.metric;
+  a.block_warps = p->block_warps;
+  a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
+  a.k = p->k;
+  a.out_ids = d_knn_ids;
+  a.out_dis = d_knn_dist;
+  a.rho = d_density;
+  a.rkey = d_rank_key;
+  a.density_fn = p->density;
+  a.fb_list = sc.fb_list;
+  a.fb_cnt = sc.fb_cnt;
+  a.err = sc.err;
+  a.work = sc.work;
+  if (reduced) {
+    // walk the reduced rows, keep the K best candidates, re-rank them in FP32
+    a.mode = MODE_RAW;
+    a.k = K;
+    a.out_ids = sc.rr_ids;
+    a.out_dis = sc.rr_dis;
+    a.out_cnt = sc.rr_cnt;
+    if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
+    e = launch_rerank_knn(fv, sc.rr_ids, sc.rr_cnt, K, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key,
+                          p->density, sc.fb_list, sc.fb_cnt, st);
+    if ((s = cuda_status(e, "FP32 re-rank"))) return s;
+  } else {
+    if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
+  }
+  // points whose search returned fewer than k: exact k-NN by brute force
+  e = launch_bruteforce_knn(fv, sc.fb_list, sc.fb_cnt, dv.n, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key,
+                            p->density, sc.err, st);
+  if ((s = cuda_status(e, "brute-force k-NN"))) return s;
+  if (p->normalize_density) {
+    if ((e = cudaMemcpyAsync(sc.raw, d_density, (size_t)dv.n * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return cuda_status(e, "copy");
+    unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
+    k_normalize_density<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, sc.raw, d_density, d_rank_key); note_launch();
+    if ((s = cuda_status(cudaGetLastError(), "normalize"))) return s;
+  }
+  return read_err(sc.err, st);
 }
 
 }  // namespace pecann
@@ -336,77 +418,28 @@ pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, c
   DataView dv, fv;
   pecann_status s = check_dataset(ds, &dv, &fv);
   if (s) return s;
-  if ((s = check_params(p, dv.n))) return s;
-  if (!d_graph || !d_knn_ids || !d_knn_dist || !d_density || !d_rank_key || !ws)
-    return set_last_error("NULL pointer"), PECANN_EINVAL;
-  if (p->density < 0 || p->density > 3) return set_last_error("bad density function"), PECANN_EINVAL;
+  if ((s = check_density_args(dv, d_graph, p, d_knn_ids, d_knn_dist, d_density, d_rank_key))) return s;
+  if (!ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
   const bool reduced = is_reduced(dv.dtype);
   const int K = reduced ? rerank_k_of(p) : 0;
-  if (reduced && K > p->L_search) return set_last_error("rerank_k must be in k..L_search"), PECANN_EINVAL;
   if (ws_bytes < HDR + density_bytes(dv.n, K)) return set_last_error("workspace too small"), PECANN_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
   WsHeader* h = (WsHeader*)ws;
   uint8_t* w = (uint8_t*)ws + HDR;
-  int32_t* fb_list = (int32_t*)w;
-  float* raw = (float*)(w + al((size_t)dv.n * 4));
+  DensityScratch sc;
+  sc.fb_list = (int32_t*)w;
+  sc.raw = (float*)(w + al((size_t)dv.n * 4));
+  sc.fb_cnt = &h->counts[0];
+  sc.err = &h->err;
+  sc.work = p->collect_work ? h->work : nullptr;
+  if (reduced) {
+    sc.rr_ids = (int32_t*)(w + 2 * al((size_t)dv.n * 4));
+    sc.rr_dis = (float*)((uint8_t*)sc.rr_ids + al((size_t)dv.n * K * 4));
+    sc.rr_cnt = (int32_t*)((uint8_t*)sc.rr_dis + al((size_t)dv.n * K * 4));
+  }
   cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
   if (e != cudaSuccess) return cuda_status(e, "memset");
-  SearchArgs a;
-  memset(&a, 0, sizeof(a));
-  a.X = dv.X;
-  a.row_bytes = dv.row_bytes;
-  a.n = dv.n;
-  a.C = dv.C;
-  a.G = d_graph;
-  a.R = p->R;
-  a.queries = nullptr;
-  a.nq = dv.n;
-  a.Lw = p->L_search;
-  a.log2h = log2_hash(p, a.Lw);
-  a.stage = (p->R + 31) & ~31;
-  a.mode = MODE_KNN;
-  a.metric = dv.metric;
-  a.block_warps = p->block_warps;
-  a.warp_bytes = search_warp_bytes(a.Lw, a.log2h, a.stage, 0, false);
-  a.k = p->k;
-  a.out_ids = d_knn_ids;
-  a.out_dis = d_knn_dist;
-  a.rho = d_density;
-  a.rkey = d_rank_key;
-  a.density_fn = p->density;
-  a.fb_list = fb_list;
-  a.fb_cnt = &h->counts[0];
-  a.err = &h->err;
-  a.work = p->collect_work ? h->work : nullptr;
-  if (reduced) {
-    // walk the BF16 rows, keep the K best candidates, re-rank them in FP32
-    int32_t* rr_ids = (int32_t*)(w + 2 * al((size_t)dv.n * 4));
-    float* rr_dis = (float*)((uint8_t*)rr_ids + al((size_t)dv.n * K * 4));
-    int32_t* rr_cnt = (int32_t*)((uint8_t*)rr_dis + al((size_t)dv.n * K * 4));
-    a.mode = MODE_RAW;
-    a.k = K;
-    a.out_ids = rr_ids;
-    a.out_dis = rr_dis;
-    a.out_cnt = rr_cnt;
-    if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
-    e = launch_rerank_knn(fv, rr_ids, rr_cnt, K, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key, p->density,
-                          fb_list, &h->counts[0], st);
-    if ((s = cuda_status(e, "FP32 re-rank"))) return s;
-  } else {
-    if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
-  }
-  // points whose search returned fewer than k: exact k-NN by brute force
-  e = launch_bruteforce_knn(fv, fb_list, &h->counts[0], dv.n, p->k, d_knn_ids, d_knn_dist, d_density,
-                            d_rank_key, p->density, &h->err, st);
-  if ((s = cuda_status(e, "brute-force k-NN"))) return s;
-  if (p->normalize_density) {
-    if ((e = cudaMemcpyAsync(raw, d_density, (size_t)dv.n * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-      return cuda_status(e, "copy");
-    unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
-    k_normalize_density<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, raw, d_density, d_rank_key); note_launch();
-    if ((s = cuda_status(cudaGetLastError(), "normalize"))) return s;
-  }
-  return PECANN_OK;
+  return run_density(dv, fv, d_graph, p, d_knn_ids, d_knn_dist, d_density, d_rank_key, sc, st);
 }
 
 pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d_graph, const pecann_params* p,

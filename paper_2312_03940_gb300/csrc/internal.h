@@ -129,6 +129,38 @@ cudaError_t launch_rerank_knn(const DataView& f32, const int32_t* cand, const in
 cudaError_t launch_rerank_dep(const DataView& f32, const int32_t* list, int64_t m, const int32_t* cand,
                               const int32_t* cnt, int K, int32_t* lam, float* delta, cudaStream_t st);
 
+// Argument checks and status helpers of the C ABI (abi.cu), shared by
+// every entry point so that their rules cannot drift apart.
+// check_dataset fills the view of the rows; f32 (optional) gets the FP32
+// rows: the same view for FP32 / U8 data, data_f32 for BF16 / FP8.
+pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataView* f32 = nullptr);
+pecann_status check_params(const pecann_params* p, int64_t n);
+pecann_status check_density_args(const DataView& dv, const int32_t* d_graph, const pecann_params* p,
+                                 const int32_t* d_knn_ids, const float* d_knn_dist, const float* d_density,
+                                 const float* d_rank_key);
+pecann_status cuda_status(cudaError_t e, const char* what);
+// Reads the device error word (synchronises `st`); PECANN_EINTERNAL if set.
+pecann_status read_err(int* d_err, cudaStream_t st);
+int log2_hash(const pecann_params* p, int Lw);
+int rerank_k_of(const pecann_params* p);
+
+// Device scratch of one k-NN + density pass. fb_list and raw hold n entries
+// each; rr_* (n x rerank_k ids and distances, n counts) only for BF16 / FP8
+// rows (NULL otherwise); work is optional.
+struct DensityScratch {
+  int32_t* fb_list = nullptr;
+  float* raw = nullptr;
+  int32_t* fb_cnt = nullptr;
+  int* err = nullptr;
+  unsigned long long* work = nullptr;
+  int32_t* rr_ids = nullptr;
+  float* rr_dis = nullptr;
+  int32_t* rr_cnt = nullptr;
+};
+pecann_status run_density(const DataView& dv, const DataView& fv, const int32_t* d_graph, const pecann_params* p,
+                          int32_t* d_knn_ids, float* d_knn_dist, float* d_density, float* d_rank_key,
+                          const DensityScratch& sc, cudaStream_t st);
+
 int num_sms();
 // Counts the kernels the library launches (reported by pecann_kernel_launches).
 void note_launch();

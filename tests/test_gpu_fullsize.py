@@ -53,28 +53,63 @@ def test_fullsize_search_density_and_dependents_against_the_oracle(data):
         assert (dist[q] == oracle.out_dist(P, od)).all(), q
     # 2) round 0 for sampled points, recomputed by the oracle: its own k-NN of
     #    the point and the densities of those neighbours from their own searches
-    def kth_density(i):
-        _, d_ = oracle.greedy_search(P, G, int(i), [int(i)], L=L, k=K)
-        return np.float32(1.0) / np.float32(oracle.out_dist(P, d_)[-1])
+    memo = {}
 
-    for i in synth.sample_ids(N, 30, seed=8):
+    def kth_density(i):
+        if i not in memo:
+            _, d_ = oracle.greedy_search(P, G, int(i), [int(i)], L=L, k=K)
+            memo[i] = np.float32(1.0) / np.float32(oracle.out_dist(P, d_)[-1])
+        return memo[i]
+
+    def ranks_above(kj, j, ki, i):
+        return kj > ki or (kj == ki and j < i)
+
+    stats = dep["stats"]
+    has = lam >= 0
+    top = int(np.flatnonzero(~has)[0]) if (~has).any() else -1
+
+    def check_point(i):
+        """lambda_i from the oracle: round 0 over its k-NN list, then the
+        doubling rounds the GPU ran (k_dep = L 2^r), then the exact tail."""
         oi, _ = oracle.greedy_search(P, G, int(i), [int(i)], L=L, k=K)
-        ki = kth_density(i)
+        ki = kth_density(int(i))
         assert key[i] == ki
-        first = -1
         for j in oi:
-            kj = kth_density(j)
-            if kj > ki or (kj == ki and j < i):
-                first = int(j)
-                break
-        if first >= 0:
-            assert lam[i] == first, i
+            if ranks_above(kth_density(int(j)), int(j), ki, int(i)):
+                assert lam[i] == int(j), i
+                return "round 0"
+        if i == top:
+            return "maximum"
+        for r in range(int(stats[0])):
+            kd = L << r
+            ci, _ = oracle.greedy_search(P, G, int(i), [int(i)], L=kd, k=kd)
+            for j in ci:
+                if ranks_above(kth_density(int(j)), int(j), ki, int(i)):
+                    assert lam[i] == int(j), (i, r)
+                    return f"round {r + 1}"
+        # not found by any round: the brute-force tail's exact answer, the
+        # closest point ranked above i (integer distances; ranks by the keys
+        # whose values the samples above pin to the oracle's)
+        d2 = ((X.astype(np.int32) - X[i].astype(np.int32)) ** 2).sum(1, dtype=np.int64)
+        above = (key > key[i]) | ((key == key[i]) & (np.arange(N) < i))
+        d2 = np.where(above, d2, np.iinfo(np.int64).max)
+        assert lam[i] == int(np.argmin(d2)), i
+        return "tail"
+
+    seen = set()
+    for i in synth.sample_ids(N, 30, seed=8):
+        seen.add(check_point(int(i)))
+    # points the GPU did not resolve in round 0 (their dependent point is not
+    # in their k-NN list): the doubling rounds and the tail, checked the same way
+    later = np.flatnonzero(has & ~(ids == lam[:, None]).any(1))
+    assert len(later) > 0
+    for i in np.random.default_rng(11).choice(later, size=min(4, len(later)), replace=False):
+        seen.add(check_point(int(i)))
+    assert seen - {"round 0", "maximum"}, seen
     # 3) properties at full size: every dependent point ranks strictly above
     #    its point, exactly one point (the maximum) has none, delta is the
     #    oracle's distance of the pair
-    has = lam >= 0
     assert (~has).sum() == 1
-    top = int(np.flatnonzero(~has)[0])
     order = exact.rank_order(key.astype(np.float64))
     assert order[0] == top
     rank = np.empty(N, np.int64)
