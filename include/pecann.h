@@ -105,6 +105,15 @@ typedef enum {
                                   (pecann_cluster_sweep only)            */
 } pecann_center_fn;
 
+/* k-NN index of the density and dependent-point searches (Sec. 5.1). */
+typedef enum {
+  PECANN_INDEX_GRAPH = 0,      /* greedy beam search (Algorithm 1) on the given graph        */
+  PECANN_INDEX_BRUTE_FORCE = 1 /* no index: exact k-NN and dependent points over all points,
+                                  screened on the tensor cores (BF16 rows, FP32 accumulation)
+                                  and decided exactly on the canonical distance; IP or L2,
+                                  d a multiple of 8, k <= 63                               */
+} pecann_index;
+
 /* Parameters of the method. pecann_params_default() fills the paper's
    defaults; every field is read by the calls named beside it. */
 typedef struct {
@@ -136,7 +145,9 @@ typedef struct {
                                 (0: min(L_search, 4k); must be >= k)         density          */
   int32_t block_warps;       /* warps per block of the search kernel (1, 2, 4 or 8; 0 =
                                 automatic). Like hash_slots it changes speed, never results */
-  int32_t reserved2;
+  int32_t index;             /* PECANN_INDEX_GRAPH (the Vamana graph given to the call) or
+                                PECANN_INDEX_BRUTE_FORCE (no index, exact; the graph may be
+                                NULL)                                      density, dependent */
   uint64_t seed;             /* insertion order when none is given         build              */
 } pecann_params;
 

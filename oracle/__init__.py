@@ -66,6 +66,9 @@ def _load():
         _lib.orc_greedy_search.restype = i64
         _lib.orc_knn_density.argtypes = [P, vp, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, ctypes.c_int]
         _lib.orc_knn_density.restype = ctypes.c_int
+        _lib.orc_knn_density_rows.argtypes = [P, vp, i32, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp,
+                                              ctypes.c_int]
+        _lib.orc_knn_density_rows.restype = ctypes.c_int
         _lib.orc_dependent_points.argtypes = [P, vp, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp,
                                               ctypes.c_int]
         _lib.orc_dependent_points.restype = ctypes.c_int
@@ -148,34 +151,58 @@ def greedy_search(P: Points, G: np.ndarray, q: int, S, L: int, k: int, visit_cap
 def knn_density(P: Points, G: np.ndarray, L: int, k: int, density: int = DENS_KTH,
                 normalize: bool = False, threads: int | None = None):
     """k-NN of every point on G (start = the point itself) and its density.
+    G None: no index (Sec. 5.1, brute force), the exact k-NN of every point.
     Returns dict ids (n,k) int32, dist (n,k) f32, rho (n,) f32, key (n,) f32,
     fallback (n,) int32."""
-    G = np.ascontiguousarray(G, dtype=np.int32)
+    G = np.ascontiguousarray(G, dtype=np.int32) if G is not None else None
     n = P.n
     ids = np.empty((n, k), np.int32)
     dist = np.empty((n, k), np.float32)
     rho = np.empty(n, np.float32)
     key = np.empty(n, np.float32)
     fb = np.empty(n, np.int32)
-    rc = _load().orc_knn_density(P.ptr, _p(G), G.shape[1], L, k, density, int(normalize), _p(ids), _p(dist),
+    rc = _load().orc_knn_density(P.ptr, _p(G) if G is not None else None, G.shape[1] if G is not None else 0, L,
+                                 k, density, int(normalize), _p(ids), _p(dist),
                                  _p(rho), _p(key), _p(fb), threads or default_threads())
     if rc:
         raise ValueError("orc_knn_density: bad arguments")
     return dict(ids=ids, dist=dist, rho=rho, key=key, fallback=fb)
 
 
+def knn_density_rows(P: Points, G, rows, L: int, k: int, density: int = DENS_KTH, threads: int | None = None):
+    """knn_density for the listed points only (no normalisation). G None: the
+    brute-force index. Returns dict ids (m,k), dist (m,k), rho (m,), key (m,),
+    fallback (m,)."""
+    G = np.ascontiguousarray(G, dtype=np.int32) if G is not None else None
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    m = len(rows)
+    ids = np.empty((m, k), np.int32)
+    dist = np.empty((m, k), np.float32)
+    rho = np.empty(m, np.float32)
+    key = np.empty(m, np.float32)
+    fb = np.empty(m, np.int32)
+    rc = _load().orc_knn_density_rows(P.ptr, _p(G) if G is not None else None, G.shape[1] if G is not None else 0,
+                                      L, k, density, _p(rows), m, _p(ids), _p(dist), _p(rho), _p(key), _p(fb),
+                                      threads or default_threads())
+    if rc:
+        raise ValueError("orc_knn_density_rows: bad arguments")
+    return dict(ids=ids, dist=dist, rho=rho, key=key, fallback=fb)
+
+
 def dependent_points(P: Points, G: np.ndarray, key: np.ndarray, knn_ids: np.ndarray, Ld: int,
                      threshold: int = 300, max_rounds: int = 30, max_beam: int = 1 << 30,
                      threads: int | None = None):
-    """Algorithm 3. Returns dict lam (n,) int32, delta (n,) f32, stats."""
-    G = np.ascontiguousarray(G, dtype=np.int32)
+    """Algorithm 3. G None: no index (Sec. 5.1, brute force), FindKnn is the
+    exact k_dep-NN. Returns dict lam (n,) int32, delta (n,) f32, stats."""
+    G = np.ascontiguousarray(G, dtype=np.int32) if G is not None else None
     key = np.ascontiguousarray(key, dtype=np.float32)
     knn_ids = np.ascontiguousarray(knn_ids, dtype=np.int32)
     n, k = knn_ids.shape
     lam = np.empty(n, np.int32)
     delta = np.empty(n, np.float32)
     stats = np.zeros(64, np.int64)
-    _load().orc_dependent_points(P.ptr, _p(G), G.shape[1], _p(key), _p(knn_ids), k, Ld, threshold, max_rounds,
+    _load().orc_dependent_points(P.ptr, _p(G) if G is not None else None, G.shape[1] if G is not None else 0,
+                                 _p(key), _p(knn_ids), k, Ld, threshold, max_rounds,
                                  max_beam, _p(lam), _p(delta), _p(stats), threads or default_threads())
     rounds = int(stats[0])
     return dict(lam=lam, delta=delta, rounds=rounds, unfinished_round0=int(stats[1]),

@@ -459,35 +459,44 @@ typedef struct {
   float* key;
   int32_t* fallback;
   search_ws* ws;
+  const int64_t* rows; /* NULL: row u is point u; else the point of output row u */
 } knn_ctx;
 
-static void knn_body(void* c, int64_t i, int tid) {
+static void knn_body(void* c, int64_t u, int tid) {
   knn_ctx* x = (knn_ctx*)c;
   int32_t k = x->k;
+  const int64_t i = x->rows ? x->rows[u] : u;
   item* out = (item*)malloc(sizeof(item) * (size_t)k);
   int32_t S[1] = {(int32_t)i};
-  /* N_i <- G.Find-Knn(x_i, k), start set = {x_i} */
-  int64_t cnt = greedy_search(x->P, x->G, x->R, i, S, 1, x->L, k, &x->ws[tid], out, NULL, NULL);
+  int64_t cnt;
+  if (x->G == NULL) {
+    /* no index (Sec. 5.1, brute force): the exact k-NN over P \ {x_i} */
+    cnt = brute_force_knn(x->P, i, k, out);
+  } else {
+    /* N_i <- G.Find-Knn(x_i, k), start set = {x_i} */
+    cnt = greedy_search(x->P, x->G, x->R, i, S, 1, x->L, k, &x->ws[tid], out, NULL, NULL);
+  }
   if (cnt < k) {
     /* fewer than k points returned: exact k-NN by brute force */
     cnt = brute_force_knn(x->P, i, k, out);
-    x->fallback[i] = 1;
+    x->fallback[u] = 1;
   }
   float dis[4096], D[4096];
   for (int32_t t = 0; t < k; t++) {
-    x->ids[i * k + t] = out[t].id;
+    x->ids[u * k + t] = out[t].id;
     dis[t] = out[t].dis;
     D[t] = orc_out_dist(x->P, out[t].dis);
-    x->dist[i * k + t] = D[t];
+    x->dist[u * k + t] = D[t];
   }
   /* rho_i <- F_density(x_i, N_i) */
-  density_of(x->P, x->fn, k, dis, D, &x->rho[i], &x->key[i]);
+  density_of(x->P, x->fn, k, dis, D, &x->rho[u], &x->key[u]);
   free(out);
 }
 
 /*
  * k-NN of every point on graph G (beam width L, start set {x_i}), followed by
- * its density. Outputs: ids/dist n x k (sorted by (dis, id)), rho n, key n
+ * its density. G == NULL is the brute-force index of Sec. 5.1: every k-NN is
+ * the exact one over P \ {x_i} (L unused). Outputs: ids/dist n x k (sorted by (dis, id)), rho n, key n
  * (rank key), fallback n (1 where the graph search returned < k points).
  * normalize != 0 applies rho'_i = rho_i k / sum_{j in N_i} rho_j (Sec. 4.2).
  * Requires n > k and k <= 4096.
@@ -500,7 +509,7 @@ int orc_knn_density(const orc_points* P, const int32_t* G, int32_t R, int32_t L,
   search_ws* ws = (search_ws*)malloc(sizeof(search_ws) * nthreads);
   for (int t = 0; t < nthreads; t++) ws_init(&ws[t], P->n);
   memset(fallback, 0, sizeof(int32_t) * (size_t)P->n);
-  knn_ctx c = {P, G, R, L, k, fn, ids, dist, rho, key, fallback, ws};
+  knn_ctx c = {P, G, R, L, k, fn, ids, dist, rho, key, fallback, ws, NULL};
   parallel_for(P->n, nthreads, knn_body, &c);
   for (int t = 0; t < nthreads; t++) ws_free(&ws[t]);
   free(ws);
@@ -515,6 +524,27 @@ int orc_knn_density(const orc_points* P, const int32_t* G, int32_t R, int32_t L,
     }
     free(raw);
   }
+  return 0;
+}
+
+/*
+ * The k-NN and density of the m listed points only (rows[u] for output row
+ * u): the same steps as orc_knn_density (graph G, or G == NULL for the
+ * brute-force index), without the normalisation, which needs every point.
+ * Used to time the method on a sample of a large point set.
+ */
+int orc_knn_density_rows(const orc_points* P, const int32_t* G, int32_t R, int32_t L, int32_t k, int32_t fn,
+                         const int64_t* rows, int64_t m, int32_t* ids, float* dist, float* rho, float* key,
+                         int32_t* fallback, int nthreads) {
+  if (k < 1 || k > 4096 || P->n <= k) return 1;
+  if (nthreads < 1) nthreads = 1;
+  search_ws* ws = (search_ws*)malloc(sizeof(search_ws) * nthreads);
+  for (int t = 0; t < nthreads; t++) ws_init(&ws[t], P->n);
+  memset(fallback, 0, sizeof(int32_t) * (size_t)m);
+  knn_ctx c = {P, G, R, L, k, fn, ids, dist, rho, key, fallback, ws, rows};
+  parallel_for(m, nthreads, knn_body, &c);
+  for (int t = 0; t < nthreads; t++) ws_free(&ws[t]);
+  free(ws);
   return 0;
 }
 
@@ -566,9 +596,14 @@ static void dep_round_body(void* c, int64_t u, int tid) {
   item* out = (item*)malloc(sizeof(item) * (size_t)x->kdep);
   int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * (size_t)x->kdep);
   int32_t S[1] = {(int32_t)i};
-  /* N_candidates <- G.FindKnn(i, k_dep): beam width k_dep */
-  int64_t cnt = greedy_search(x->P, x->G, x->R, i, S, 1, x->kdep, x->kdep, &x->ws[tid], out,
-                              NULL, NULL);
+  int64_t cnt;
+  if (x->G == NULL) {
+    /* no index (Sec. 5.1, brute force): FindKnn is the exact k_dep-NN */
+    cnt = brute_force_knn(x->P, i, x->kdep, out);
+  } else {
+    /* N_candidates <- G.FindKnn(i, k_dep): beam width k_dep */
+    cnt = greedy_search(x->P, x->G, x->R, i, S, 1, x->kdep, x->kdep, &x->ws[tid], out, NULL, NULL);
+  }
   for (int64_t t = 0; t < cnt; t++) cand[t] = out[t].id;
   x->lam[i] = dp_bruteforce(x->P, x->key, i, cand, cnt, &x->dis[i]);
   free(cand);
@@ -587,7 +622,8 @@ static void dep_tail_body(void* c, int64_t u, int tid) {
 
 /*
  * ComputeDepPts (Algorithm 3). key is the rank key of every point, knn the
- * n x k neighbour lists. Round 0 searches N_i; then, while more than
+ * n x k neighbour lists. G == NULL is the brute-force index of Sec. 5.1:
+ * FindKnn(i, k_dep) returns the exact k_dep nearest points. Round 0 searches N_i; then, while more than
  * `threshold` points are unfinished, each unfinished point (the global
  * maximum excluded) runs FindKnn with beam width and result size k_dep
  * (k_dep = Ld, doubling each round). The doubling stops early after

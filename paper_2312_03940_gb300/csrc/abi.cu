@@ -154,6 +154,10 @@ pecann_status read_err(int* d_err, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "error readback");
+  if (h == ERR_TIMEOUT) {
+    set_last_error("a pipeline wait of the tensor-core screen ran past its limit");
+    return PECANN_ETIMEOUT;
+  }
   if (h) {
     set_last_error(h == ERR_BAD_ID ? "graph or query id out of range"
                                    : (h == ERR_NO_PROGRESS ? "search made no progress" : "capacity exceeded"));
@@ -183,18 +187,49 @@ static size_t dep_bytes(int64_t n, bool reduced) {
   if (reduced) b += al((size_t)n * DEP_RERANK * 4) + al((size_t)n * 4);
   return b;
 }
+// Brute-force index: the k-NN / dependent pieces above, then its own scratch.
+static size_t bf_density_offset(int64_t n) { return 2 * al((size_t)n * 4); }
+static size_t bf_dep_offset(int64_t n) { return 2 * al((size_t)n * 4) + al((size_t)n * 8); }
+
+// The brute-force index reads BF16 copies of the rows through TMA (rows of
+// d * 2 bytes, a multiple of 16) and keeps 64 candidates per query.
+pecann_status check_index(const DataView& dv, const pecann_params* p) {
+  if (p->index != PECANN_INDEX_GRAPH && p->index != PECANN_INDEX_BRUTE_FORCE)
+    return set_last_error("index must be PECANN_INDEX_GRAPH or PECANN_INDEX_BRUTE_FORCE"), PECANN_EINVAL;
+  if (p->index == PECANN_INDEX_BRUTE_FORCE) {
+    if (dv.d % 8) return set_last_error("the brute-force index needs d to be a multiple of 8"), PECANN_EUNSUPPORTED;
+    if (p->k > 63) return set_last_error("the brute-force index supports k <= 63"), PECANN_EUNSUPPORTED;
+  }
+  return PECANN_OK;
+}
 
 pecann_status check_density_args(const DataView& dv, const int32_t* d_graph, const pecann_params* p,
                                  const int32_t* d_knn_ids, const float* d_knn_dist, const float* d_density,
                                  const float* d_rank_key) {
   pecann_status s = check_params(p, dv.n);
   if (s) return s;
-  if (!d_graph || !d_knn_ids || !d_knn_dist || !d_density || !d_rank_key)
+  if ((s = check_index(dv, p))) return s;
+  if ((!d_graph && p->index == PECANN_INDEX_GRAPH) || !d_knn_ids || !d_knn_dist || !d_density || !d_rank_key)
     return set_last_error("NULL pointer"), PECANN_EINVAL;
   if (p->density < 0 || p->density > 3) return set_last_error("bad density function"), PECANN_EINVAL;
   if (is_reduced(dv.dtype) && rerank_k_of(p) > p->L_search)
     return set_last_error("rerank_k must be in k..L_search"), PECANN_EINVAL;
   return PECANN_OK;
+}
+
+// The optional normalisation (Sec. 4.2), then the error word.
+static pecann_status finish_density(const DataView& dv, const pecann_params* p, const int32_t* d_knn_ids,
+                                    float* d_density, float* d_rank_key, const DensityScratch& sc, cudaStream_t st) {
+  pecann_status s;
+  cudaError_t e;
+  if (p->normalize_density) {
+    if ((e = cudaMemcpyAsync(sc.raw, d_density, (size_t)dv.n * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return cuda_status(e, "copy");
+    unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
+    k_normalize_density<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, sc.raw, d_density, d_rank_key); note_launch();
+    if ((s = cuda_status(cudaGetLastError(), "normalize"))) return s;
+  }
+  return read_err(sc.err, st);
 }
 
 // k-NN + density (Algorithm 2 lines 2-4) on checked arguments: the beam
@@ -208,9 +243,21 @@ pecann_status run_density(const DataView& dv, const DataView& fv, const int32_t*
                           const DensityScratch& sc, cudaStream_t st) {
   const bool reduced = is_reduced(dv.dtype);
   const int K = reduced ? rerank_k_of(p) : 0;
-  if (reduced && !sc.rr_ids) return set_last_error("no re-rank scratch for BF16 / FP8 rows"), PECANN_EUNSUPPORTED;
   pecann_status s;
   cudaError_t e;
+  if (p->index == PECANN_INDEX_BRUTE_FORCE) {
+    // exact k-NN by the tensor-core screen and the exact re-rank (Sec. 5.1,
+    // brute force); points it leaves go through the SIMT brute force below
+    if (!sc.bf_ws) return set_last_error("no scratch for the brute-force index"), PECANN_EUNSUPPORTED;
+    if ((s = run_density_bf(fv, p, d_knn_ids, d_knn_dist, d_density, d_rank_key, sc.fb_list, sc.fb_cnt, sc.err,
+                            sc.bf_ws, sc.bf_counts, st)))
+      return s;
+    e = launch_bruteforce_knn(fv, sc.fb_list, sc.fb_cnt, dv.n, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key,
+                              p->density, sc.err, st);
+    if ((s = cuda_status(e, "brute-force k-NN"))) return s;
+    return finish_density(dv, p, d_knn_ids, d_density, d_rank_key, sc, st);
+  }
+  if (reduced && !sc.rr_ids) return set_last_error("no re-rank scratch for BF16 / FP8 rows"), PECANN_EUNSUPPORTED;
   SearchArgs a;
   memset(&a, 0, sizeof(a));
   a.X = dv.X;
@@ -246,7 +293,7 @@ pecann_status run_density(const DataView& dv, const DataView& fv, const int32_t*
     a.out_dis = sc.rr_dis;
     a.out_cnt = sc.rr_cnt;
     if ((s = cuda_status(launch_search(dv, a, st), "k-NN search"))) return s;
-    e = launch_rerank_knn(fv, sc.rr_ids, sc.rr_cnt, K, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key,
+    e = launch_rerank_knn(fv, nullptr, dv.n, sc.rr_ids, sc.rr_cnt, K, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key,
                           p->density, sc.fb_list, sc.fb_cnt, st);
     if ((s = cuda_status(e, "FP32 re-rank"))) return s;
   } else {
@@ -256,14 +303,16 @@ pecann_status run_density(const DataView& dv, const DataView& fv, const int32_t*
   e = launch_bruteforce_knn(fv, sc.fb_list, sc.fb_cnt, dv.n, p->k, d_knn_ids, d_knn_dist, d_density, d_rank_key,
                             p->density, sc.err, st);
   if ((s = cuda_status(e, "brute-force k-NN"))) return s;
-  if (p->normalize_density) {
-    if ((e = cudaMemcpyAsync(sc.raw, d_density, (size_t)dv.n * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-      return cuda_status(e, "copy");
-    unsigned blocks = (unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8);
-    k_normalize_density<<<blocks, 256, 0, st>>>(dv.n, p->k, d_knn_ids, sc.raw, d_density, d_rank_key); note_launch();
-    if ((s = cuda_status(cudaGetLastError(), "normalize"))) return s;
-  }
-  return read_err(sc.err, st);
+  return finish_density(dv, p, d_knn_ids, d_density, d_rank_key, sc, st);
+}
+
+// Brute-force index: the points that took the collect pass and those left
+// to the exact SIMT kernels, as two int32 at byte offset 24 of the workspace.
+static pecann_status write_bf_counts(WsHeader* h, const int64_t* c, cudaStream_t st) {
+  const int32_t v[2] = {(int32_t)c[0], (int32_t)c[1]};
+  cudaError_t e = cudaMemcpyAsync(&h->counts[4], v, 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e, "counters");
 }
 
 }  // namespace pecann
@@ -298,6 +347,7 @@ void pecann_params_default(pecann_params* p) {
   p->build_passes = 1;
   p->rerank_k = 0;
   p->block_warps = 0;
+  p->index = PECANN_INDEX_GRAPH;
   p->seed = 0;
 }
 
@@ -327,6 +377,8 @@ pecann_status pecann_workspace_size(const pecann_dataset* ds, const pecann_param
   const bool red = is_reduced(ds->dtype);
   size_t b = density_bytes(n, red ? std::min(std::max(rerank_k_of(p), 1), 8192) : 0);
   b = std::max(b, dep_bytes(n, red));
+  if (p->index == PECANN_INDEX_BRUTE_FORCE && ds->d > 0)
+    b = std::max(b, std::max(bf_density_offset(n), bf_dep_offset(n)) + bf_ws_bytes(n, ds->d));
   b = std::max(b, cluster_ws_bytes(n));
   if (p->R >= 1 && p->L_build >= 1) {
     int vcap = p->visit_cap > 0 ? p->visit_cap : 2 * p->L_build;
@@ -421,25 +473,34 @@ pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, c
   if ((s = check_density_args(dv, d_graph, p, d_knn_ids, d_knn_dist, d_density, d_rank_key))) return s;
   if (!ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
   const bool reduced = is_reduced(dv.dtype);
-  const int K = reduced ? rerank_k_of(p) : 0;
-  if (ws_bytes < HDR + density_bytes(dv.n, K)) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  const bool bf = p->index == PECANN_INDEX_BRUTE_FORCE;
+  const int K = reduced && !bf ? rerank_k_of(p) : 0;
+  const size_t need = bf ? bf_density_offset(dv.n) + bf_ws_bytes(dv.n, dv.d) : density_bytes(dv.n, K);
+  if (ws_bytes < HDR + need) return set_last_error("workspace too small"), PECANN_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
   WsHeader* h = (WsHeader*)ws;
   uint8_t* w = (uint8_t*)ws + HDR;
   DensityScratch sc;
+  int64_t bf_counts[2] = {0, 0};
+  if (bf) {
+    sc.bf_ws = w + bf_density_offset(dv.n);
+    sc.bf_counts = bf_counts;
+  }
   sc.fb_list = (int32_t*)w;
   sc.raw = (float*)(w + al((size_t)dv.n * 4));
   sc.fb_cnt = &h->counts[0];
   sc.err = &h->err;
   sc.work = p->collect_work ? h->work : nullptr;
-  if (reduced) {
+  if (reduced && !bf) {
     sc.rr_ids = (int32_t*)(w + 2 * al((size_t)dv.n * 4));
     sc.rr_dis = (float*)((uint8_t*)sc.rr_ids + al((size_t)dv.n * K * 4));
     sc.rr_cnt = (int32_t*)((uint8_t*)sc.rr_dis + al((size_t)dv.n * K * 4));
   }
   cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
   if (e != cudaSuccess) return cuda_status(e, "memset");
-  return run_density(dv, fv, d_graph, p, d_knn_ids, d_knn_dist, d_density, d_rank_key, sc, st);
+  if ((s = run_density(dv, fv, d_graph, p, d_knn_ids, d_knn_dist, d_density, d_rank_key, sc, st))) return s;
+  if (bf) return write_bf_counts(h, bf_counts, st);
+  return PECANN_OK;
 }
 
 pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d_graph, const pecann_params* p,
@@ -450,14 +511,18 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
   pecann_status s = check_dataset(ds, &dv, &fv);
   if (s) return s;
   if ((s = check_params(p, dv.n))) return s;
-  if (!d_graph || !d_rank_key || !d_knn_ids || !d_knn_dist || !d_dep || !d_dep_dist || !ws)
+  if (!d_rank_key || !d_knn_ids || !d_knn_dist || !d_dep || !d_dep_dist || !ws)
     return set_last_error("NULL pointer"), PECANN_EINVAL;
   const bool reduced = is_reduced(dv.dtype);
   if (p->L_dep < 1 || p->max_dep_beam < 1 || p->max_dep_beam > 8192 || p->dep_threshold < 0 ||
       p->max_dep_rounds < 0)
     return set_last_error("L_dep, max_dep_beam (<= 8192), dep_threshold or max_dep_rounds out of range"),
            PECANN_EINVAL;
-  if (ws_bytes < HDR + dep_bytes(dv.n, reduced)) return set_last_error("workspace too small"), PECANN_ENOMEM;
+  if ((s = check_index(dv, p))) return s;
+  const bool bf = p->index == PECANN_INDEX_BRUTE_FORCE;
+  if (!d_graph && !bf) return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if (ws_bytes < HDR + (bf ? bf_dep_offset(dv.n) + bf_ws_bytes(dv.n, dv.d) : dep_bytes(dv.n, reduced)))
+    return set_last_error("workspace too small"), PECANN_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
   WsHeader* h = (WsHeader*)ws;
   uint8_t* w = (uint8_t*)ws + HDR;
@@ -483,6 +548,21 @@ pecann_status pecann_dependent_points(const pecann_dataset* ds, const int32_t* d
     e = cudaStreamSynchronize(st);
   if ((s = cuda_status(e, "readback"))) return s;
   stats[1] = nu;
+  if (bf) {
+    // with the brute-force index FindKnn is exact, so a doubling round finds
+    // a point's dependent point exactly when DPBruteForce over all of P
+    // would: every unfinished point goes straight to the exact search
+    int64_t c[2] = {0, 0};
+    if ((s = run_dep_bf(fv, d_rank_key, U0, nu, d_dep, d_dep_dist, &h->err, w + bf_dep_offset(dv.n), c, st)))
+      return s;
+    if ((s = read_err(&h->err, st))) return s;
+    stats[60] = c[0];
+    stats[61] = c[1];
+    stats[63] = nu;
+    if ((s = write_bf_counts(h, c, st))) return s;
+    if (h_stats) memcpy(h_stats, stats, sizeof(stats));
+    return PECANN_OK;
+  }
   int64_t kdep = p->L_dep;
   int rounds = 0;
   while (nu > p->dep_threshold && rounds < p->max_dep_rounds && kdep <= p->max_dep_beam) {

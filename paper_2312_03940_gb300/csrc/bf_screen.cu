@@ -1,0 +1,809 @@
+// The brute-force index on the tensor cores (Sec. 5.1, "Brute Force": no
+// index, exact k-NN by scanning every point; Sec. 6.1, the BruteForce
+// instance whose result is exact DPC).
+//
+// Exactness comes from a screen and an exact decision:
+//  1. Screen (k_bf_screen, tcgen05): approximate inner products of every
+//     query row against every point row from BF16 copies of the rows, FP32
+//     accumulation in TMEM. Per query the epilogue keeps the SC_KEEP best
+//     approximate keys (k-NN mode: all points but the query; dependent mode:
+//     only points ranked above the query).
+//  2. Every approximate key is within E_q of the canonical FP32 key of the
+//     pair (a bound from the BF16 rounding of both rows and the accumulation),
+//     so the exact answer is among the points whose approximate key is within
+//     2 E_q of the k-th (k-NN) or first (dependent) kept key. When the kept
+//     list reaches past that band it holds every such point; otherwise the
+//     query "overflows" and a collect pass gathers every point under its
+//     threshold into a per-query list of SC_CAP; beyond that, the exact SIMT
+//     kernels take the query.
+//  3. Decision: the existing exact re-rank kernels re-score the candidates
+//     with the canonical FP32 distance (exact integers for uint8 rows) and
+//     take the k smallest (dis, id) keys, or the closest point ranked above.
+// So the k-NN lists, densities and dependent points equal those of the exact
+// method under the canonical distance, element for element.
+//
+// Screen kernel layout (one CTA per SM, persistent over 128-query tiles):
+//   warp 0       TMA producer: 64-column chunks of the query tile (128 rows)
+//                and of the point tile (256 rows), 128-byte swizzle, into a
+//                3-stage ring of 48 KB;
+//   warp 1       TMEM owner and MMA issuer (one thread): 4 x tcgen05.mma
+//                (M 128, N 256, K 16) per chunk into one of two 256-column
+//                TMEM accumulators;
+//   warps 2..9   epilogue: two threads per query row (row = TMEM lane; the
+//                warp's lane quarter), each reading one 128-column half of a
+//                finished tile. A thread keeps the 32 smallest keys of its
+//                half in a max-heap in shared memory (slot-major, so that
+//                neighbouring threads hit neighbouring banks); a 32-column
+//                chunk is first reduced to its smallest key and only chunks
+//                that beat the heap's largest key are taken apart. At the end
+//                of a query tile the two sorted halves are merged.
+// All CTAs sweep the point tiles in the same order, so a point tile read from
+// HBM serves every CTA from L2.
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace pecann {
+
+constexpr int SC_M = 128;          // query rows per tile (TMEM lanes)
+constexpr int SC_N = 256;          // point rows per tile (TMEM columns per accumulator)
+constexpr int SC_KCH = 64;         // BF16 columns per chunk (one 128-byte swizzle row)
+constexpr int SC_STAGES = 3;
+constexpr int SC_KEEP = 64;        // kept candidates per query (two halves of SC_HALF)
+constexpr int SC_HALF = 32;        // heap entries per epilogue thread
+constexpr int SC_EPI = 256;        // epilogue threads (8 warps)
+constexpr int SC_THREADS = 64 + SC_EPI;
+constexpr uint32_t SC_A_BYTES = SC_M * SC_KCH * 2;   // 16 KB
+constexpr uint32_t SC_B_BYTES = SC_N * SC_KCH * 2;   // 32 KB
+constexpr uint32_t SC_STAGE_BYTES = SC_A_BYTES + SC_B_BYTES;
+constexpr uint64_t SC_WAIT_NS = 2000000000ull;       // 2 s per wait
+
+constexpr int SC_CAP = 1024;       // collect pass: candidates per overflowed query
+
+enum : int { SCR_KNN = 0, SCR_DEP = 1 };
+enum : int { SCR_KEEP = 0, SCR_COLLECT = 1 };
+
+struct ScreenArgs {
+  int64_t nq;             // query rows (A operand)
+  int64_t n;              // point rows (B operand)
+  int kc;                 // 64-column chunks per row
+  int k;                  // k-NN: the band is measured from the k-th kept key
+  const int32_t* qids;    // global id of query row r (NULL: r)
+  const float* pnorm2;    // squared norm of every point (L2 keys)
+  const float* pnorm;     // norm of every point, rounded up (band)
+  const float* maxnorm;   // the largest norm (device scalar)
+  const float* rank_key;  // dependent mode: rank keys of every point
+  // |approximate key - canonical key| <= E_q =
+  //   dotfac (eps_rel |x_q| M + eps_abs) + eps_sq M^2, M = max norm,
+  // dotfac = 2 for L2 (key |y|^2 - 2 <x, y>), 1 for IP (key -<x, y>)
+  float eps_rel, eps_abs, eps_sq;
+  // keep pass
+  int32_t* out_ids;       // nq x SC_KEEP (collect pass: nq x cap)
+  int32_t* out_cnt;       // nq; keep pass: -1 when the band overflowed the list
+  float* out_thr;         // keep pass: threshold for the collect pass of an overflowed row
+  int32_t* ovf_list;      // keep pass: overflowed query rows
+  int32_t* ovf_cnt;
+  // collect pass
+  const float* in_thr;    // per query row
+  int cap;
+  int* err;
+};
+
+__device__ __forceinline__ bool rank_above_key(float kj, int32_t j, float ki, int32_t i) {
+  return kj > ki || (kj == ki && j < i);
+}
+
+// Barrier of the SC_EPI epilogue threads that also ORs a flag over them.
+__device__ __forceinline__ bool epi_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, 256, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+
+// Max-heap of (key, id) per epilogue thread, slot-major: slot s of thread et
+// at [s * SC_EPI + et]. cnt < SC_HALF: filling (sift up); full: a key below
+// the root replaces it (sift down).
+__device__ __forceinline__ void heap_push(float* hk, int32_t* hi, int et, int& cnt, float key, int32_t id) {
+  if (cnt < SC_HALF) {
+    int pos = cnt++;
+    while (pos > 0) {
+      const int par = (pos - 1) >> 1;
+      const float pk = hk[par * SC_EPI + et];
+      if (!(pk < key)) break;
+      hk[pos * SC_EPI + et] = pk;
+      hi[pos * SC_EPI + et] = hi[par * SC_EPI + et];
+      pos = par;
+    }
+    hk[pos * SC_EPI + et] = key;
+    hi[pos * SC_EPI + et] = id;
+  } else {
+    int pos = 0;
+    for (;;) {
+      int c = 2 * pos + 1;
+      if (c >= SC_HALF) break;
+      float ck = hk[c * SC_EPI + et];
+      if (c + 1 < SC_HALF) {
+        const float c2 = hk[(c + 1) * SC_EPI + et];
+        if (c2 > ck) {
+          ck = c2;
+          c++;
+        }
+      }
+      if (!(ck > key)) break;
+      hk[pos * SC_EPI + et] = ck;
+      hi[pos * SC_EPI + et] = hi[c * SC_EPI + et];
+      pos = c;
+    }
+    hk[pos * SC_EPI + et] = key;
+    hi[pos * SC_EPI + et] = id;
+  }
+}
+
+// Sort a thread's heap ascending in place (heapsort).
+__device__ __forceinline__ void heap_sort(float* hk, int32_t* hi, int et, int cnt) {
+  for (int end = cnt - 1; end > 0; end--) {
+    // move the root (largest) to `end`, sift the old last entry down
+    const float key = hk[end * SC_EPI + et];
+    const int32_t id = hi[end * SC_EPI + et];
+    hk[end * SC_EPI + et] = hk[et];
+    hi[end * SC_EPI + et] = hi[et];
+    int pos = 0;
+    for (;;) {
+      int c = 2 * pos + 1;
+      if (c >= end) break;
+      float ck = hk[c * SC_EPI + et];
+      if (c + 1 < end) {
+        const float c2 = hk[(c + 1) * SC_EPI + et];
+        if (c2 > ck) {
+          ck = c2;
+          c++;
+        }
+      }
+      if (!(ck > key)) break;
+      hk[pos * SC_EPI + et] = ck;
+      hi[pos * SC_EPI + et] = hi[c * SC_EPI + et];
+      pos = c;
+    }
+    hk[pos * SC_EPI + et] = key;
+    hi[pos * SC_EPI + et] = id;
+  }
+}
+
+template <int MODE, int PASS, int METRIC>
+__global__ void __launch_bounds__(SC_THREADS, 1)
+    k_bf_screen(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, ScreenArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* hk = reinterpret_cast<float*>(ring + SC_STAGES * SC_STAGE_BYTES);  // [SC_HALF][SC_EPI]
+  int32_t* hi = reinterpret_cast<int32_t*>(hk + SC_HALF * SC_EPI);          // [SC_HALF][SC_EPI]
+  float* meta = reinterpret_cast<float*>(hi + SC_HALF * SC_EPI);           // [2][norms SC_N | keys SC_N]
+  __shared__ __align__(8) uint64_t full_bar[SC_STAGES], empty_bar[SC_STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], final_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int half_cnt[SC_EPI];   // heap sizes at the end of a query tile
+  __shared__ int row_cnt[SC_M];      // collect pass: candidates per row
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_qt = (a.nq + SC_M - 1) / SC_M;
+  const int64_t n_pt = (a.n + SC_N - 1) / SC_N;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < SC_STAGES; s++) {
+      tc::mbar_init(&full_bar[s], 1);
+      tc::mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      tc::mbar_init(&tfull_bar[b], 1);
+      tc::mbar_init(&tempty_bar[b], SC_EPI);
+    }
+    tc::mbar_init(&final_bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (threadIdx.x < SC_M) row_cnt[threadIdx.x] = 0;
+  if (warp == 1) {
+    tc::tmem_alloc(&tmem_slot, 2 * SC_N);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tc::prefetch_tmap(&ta);
+      tc::prefetch_tmap(&tb);
+      uint64_t it = 0;  // chunk loads issued
+      bool ok = true;
+      for (int64_t qt = blockIdx.x; qt < n_qt && ok; qt += gridDim.x) {
+        for (int64_t pt = 0; pt < n_pt && ok; pt++) {
+          for (int c = 0; c < a.kc; c++) {
+            const int s = (int)(it % SC_STAGES);
+            const uint32_t ph = (uint32_t)((it / SC_STAGES) & 1);
+            if (!tc::mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, SC_WAIT_NS)) {
+              ok = false;
+              break;
+            }
+            uint8_t* st = ring + (size_t)s * SC_STAGE_BYTES;
+            tc::mbar_arrive_expect_tx(&full_bar[s], SC_STAGE_BYTES);
+            tc::tma_load_2d(st, &ta, c * SC_KCH, (int32_t)(qt * SC_M), &full_bar[s]);
+            tc::tma_load_2d(st + SC_A_BYTES, &tb, c * SC_KCH, (int32_t)(pt * SC_N), &full_bar[s]);
+            it++;
+          }
+        }
+      }
+      // loads still in flight land before the block exits: wait for the last
+      // SC_STAGES issued loads (bounded, whatever the abort flag says)
+      int no_abort = 0;
+      for (uint64_t j = it > SC_STAGES ? it - SC_STAGES : 0; j < it; j++)
+        tc::mbar_wait(&full_bar[j % SC_STAGES], (uint32_t)((j / SC_STAGES) & 1), &no_abort, SC_WAIT_NS);
+      if (!ok) set_error(a.err, ERR_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(SC_M, SC_N);
+      uint64_t it = 0, tile = 0;
+      bool ok = true;
+      for (int64_t qt = blockIdx.x; qt < n_qt && ok; qt += gridDim.x) {
+        for (int64_t pt = 0; pt < n_pt && ok; pt++, tile++) {
+          const int b = (int)(tile & 1);
+          if (!tc::mbar_wait(&tempty_bar[b], (uint32_t)(((tile >> 1) & 1) ^ 1), &abort_flag, SC_WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t dacc = tmem + (uint32_t)(b * SC_N);
+          for (int c = 0; c < a.kc; c++, it++) {
+            const int s = (int)(it % SC_STAGES);
+            if (!tc::mbar_wait(&full_bar[s], (uint32_t)((it / SC_STAGES) & 1), &abort_flag, SC_WAIT_NS)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(ring + (size_t)s * SC_STAGE_BYTES), sb = sa + SC_A_BYTES;
+#pragma unroll
+            for (int k = 0; k < SC_KCH / 16; k++)
+              tc::mma_bf16(dacc, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k), idesc, (c | k) != 0);
+            tc::mma_commit(&empty_bar[s]);
+          }
+          if (ok) tc::mma_commit(&tfull_bar[b]);
+        }
+      }
+      // every MMA this thread issued completes before TMEM is released
+      tc::mma_commit(&final_bar);
+      int no_abort = 0;
+      tc::mbar_wait(&final_bar, 0, &no_abort, SC_WAIT_NS);
+      if (!ok) set_error(a.err, ERR_TIMEOUT);
+    }
+  } else {
+    // ------------------------------------------------ epilogue
+    const int et = threadIdx.x - 64;          // 0..255
+    const int rl = 32 * (warp & 3) + lane;    // row of the tile = TMEM lane (this warp's quarter)
+    const int half = (warp - 2) >> 2;         // columns [128 half, 128 half + 128) of each tile
+    const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+    const float M = __ldg(a.maxnorm);
+    uint64_t tile = 0;
+    bool ok = true;
+    for (int64_t qt = blockIdx.x; qt < n_qt && ok; qt += gridDim.x) {
+      const int64_t r = qt * SC_M + rl;
+      const bool valid = r < a.nq;
+      const int32_t qid = valid ? (a.qids ? __ldg(a.qids + r) : (int32_t)r) : -1;
+      const float qkey = (MODE == SCR_DEP && valid) ? __ldg(a.rank_key + qid) : 0.0f;
+      const float dotfac = METRIC == MET_L2 ? 2.0f : 1.0f;
+      const float E = valid ? dotfac * (a.eps_rel * __ldg(a.pnorm + qid) * M + a.eps_abs) + a.eps_sq * M * M : 0.0f;
+      // keep pass: a key is taken when below thr (the heap's largest once full)
+      float thr = PASS == SCR_COLLECT ? (valid ? __ldg(a.in_thr + r) : -INFINITY) : (valid ? INFINITY : -INFINITY);
+      int cnt = 0;
+      for (int64_t pt = 0; pt < n_pt; pt++, tile++) {
+        const int b = (int)(tile & 1);
+        const int64_t j0 = pt * SC_N;
+        // per-column data of this tile (squared norms, rank keys), double
+        // buffered by tile parity; the one barrier per tile also makes the
+        // decision to give up uniform over the epilogue threads
+        float* mt = meta + b * 2 * SC_N;
+        if (METRIC == MET_L2 || MODE == SCR_DEP) {
+          const int c = et;
+          const int64_t j = j0 + c;
+          if (METRIC == MET_L2) mt[c] = j < a.n ? __ldg(a.pnorm2 + j) : 0.0f;
+          if (MODE == SCR_DEP) mt[SC_N + c] = j < a.n ? __ldg(a.rank_key + j) : 0.0f;
+        }
+        const bool got = tc::mbar_wait(&tfull_bar[b], (uint32_t)((tile >> 1) & 1), &abort_flag, SC_WAIT_NS);
+        if (epi_sync_or(!got)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+#pragma unroll 1
+        for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * SC_N + c0), v);
+          // approximate keys, smaller = closer: -<x, y> (IP), |y|^2 - 2 <x, y> (L2)
+          float mn = INFINITY;
+#pragma unroll
+          for (int t = 0; t < 32; t++) {
+            v[t] = METRIC == MET_L2 ? __fmaf_rn(-2.0f, v[t], mt[c0 + t]) : -v[t];
+            mn = fminf(mn, v[t]);
+          }
+          const bool any = PASS == SCR_COLLECT ? (mn <= thr) : (mn < thr);
+          if (!any) continue;  // the common case once the heap is full
+          const int64_t jbase = j0 + c0;
+#pragma unroll
+          for (int t = 0; t < 32; t++) {
+            const float key = v[t];
+            const bool hit = PASS == SCR_COLLECT ? (key <= thr) : (key < thr);
+            if (!hit) continue;
+            const int64_t j = jbase + t;
+            if (j >= a.n || j == qid) continue;
+            if (MODE == SCR_DEP && !rank_above_key(mt[SC_N + c0 + t], (int32_t)j, qkey, qid)) continue;
+            if (PASS == SCR_COLLECT) {
+              const int slot = atomicAdd(&row_cnt[rl], 1);
+              if (slot < a.cap) a.out_ids[r * a.cap + slot] = (int32_t)j;
+            } else {
+              heap_push(hk, hi, et, cnt, key, (int32_t)j);
+              if (cnt == SC_HALF) thr = hk[et];
+            }
+          }
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&tempty_bar[b]);
+      }
+      if (!ok) break;
+      // ---- the row's result: both halves of the row are complete here
+      if (PASS == SCR_COLLECT) {
+        epi_sync();
+        if (half == 0) {
+          if (valid) a.out_cnt[r] = row_cnt[rl];  // > cap: the exact SIMT kernels take this row
+          row_cnt[rl] = 0;
+        }
+        epi_sync();
+        continue;
+      }
+      heap_sort(hk, hi, et, cnt);
+      half_cnt[et] = cnt;
+      epi_sync();
+      if (half == 0 && valid) {
+        // merge the two sorted halves of the row (up to SC_KEEP entries)
+        const int p2 = et + 128;
+        const int n0 = cnt, n1 = half_cnt[p2];
+        int i0 = 0, i1 = 0, m = 0;
+        const int ref = MODE == SCR_KNN ? a.k - 1 : 0;
+        float ref_key = INFINITY;
+        int32_t* out = a.out_ids + r * SC_KEEP;
+        while (i0 < n0 || i1 < n1) {
+          const bool take0 = i1 >= n1 || (i0 < n0 && hk[i0 * SC_EPI + et] <= hk[i1 * SC_EPI + p2]);
+          const float kk = take0 ? hk[i0 * SC_EPI + et] : hk[i1 * SC_EPI + p2];
+          const int32_t id = take0 ? hi[i0 * SC_EPI + et] : hi[i1 * SC_EPI + p2];
+          if (take0) i0++; else i1++;
+          if (m == ref) ref_key = kk;
+          out[m++] = id;
+        }
+        // complete when each half either kept every point it saw, or its
+        // largest kept key lies beyond the band around the reference key
+        const float lim = ref_key + 2.0f * E;
+        const bool c0ok = n0 < SC_HALF || hk[(n0 - 1) * SC_EPI + et] > lim;
+        const bool c1ok = n1 < SC_HALF || hk[(n1 - 1) * SC_EPI + p2] > lim;
+        if (m <= ref || (c0ok && c1ok)) {
+          a.out_cnt[r] = m;
+        } else {
+          a.out_cnt[r] = -1;
+          a.out_thr[r] = lim;
+          a.ovf_list[atomicAdd(a.ovf_cnt, 1)] = (int32_t)r;
+        }
+      }
+      epi_sync();
+    }
+    if (!ok) set_error(a.err, ERR_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * SC_N);
+  }
+}
+
+// ---------------------------------------------------------------- helpers
+
+// BF16 copy of FP32 or uint8 rows (round to nearest even; uint8 values are
+// exact in BF16).
+__global__ void k_rows_to_bf16(const uint8_t* X, int dtype, int64_t total, __nv_bfloat16* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = dtype == DT_F32 ? reinterpret_cast<const float*>(X)[i] : (float)X[i];
+    out[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// Norm (rounded up) and squared norm of every row, and the largest norm.
+// The sum of squares is taken in double: exact for uint8 rows (integers
+// below 2^53), and within one FP32 rounding for FP32 rows.
+__global__ void k_row_norms(const uint8_t* X, int dtype, int64_t n, int d, int64_t row_bytes, float* nrm,
+                            float* nrm2, unsigned* maxbits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < n; i += nw) {
+    double s = 0.0;
+    const uint8_t* row = X + i * row_bytes;
+    for (int c = lane; c < d; c += 32) {
+      const double v = dtype == DT_F32 ? (double)reinterpret_cast<const float*>(row)[c] : (double)row[c];
+      s += v * v;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
+    if (lane == 0) {
+      const float nr = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+      nrm2[i] = __double2float_rn(s);
+      nrm[i] = nr;
+      atomicMax(maxbits, __float_as_uint(nr));  // non-negative floats order like their bits
+    }
+  }
+}
+
+// Contiguous BF16 copy of the listed rows (the query operand of the
+// dependent and collect passes). d is a multiple of 8: 16-byte pieces.
+__global__ void k_gather_bf16(const __nv_bfloat16* rows, int d, const int32_t* list, int64_t m,
+                              __nv_bfloat16* out) {
+  const int64_t per = d / 8;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m * per; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = i / per, c = i % per;
+    reinterpret_cast<uint4*>(out)[u * per + c] =
+        __ldg(reinterpret_cast<const uint4*>(rows) + (int64_t)list[u] * per + c);
+  }
+}
+
+// The overflowed rows [off, off + m) of a keep pass: their query ids and
+// collect thresholds, contiguous.
+__global__ void k_overflow_rows(const int32_t* ovf, int64_t off, int64_t m, const int32_t* qids, const float* thr,
+                                int32_t* out_ids, float* out_thr) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t row = ovf[off + i];
+    out_ids[i] = qids ? qids[row] : row;
+    out_thr[i] = thr[row];
+  }
+}
+
+// Rows of a collect pass beyond its capacity: their query ids go to the exact
+// SIMT list, and their count becomes -1 so that the re-rank skips them.
+__global__ void k_collect_overflow(int32_t* cnt, int64_t m, int cap, const int32_t* qids, int32_t* fb,
+                                   int32_t* fb_cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    if (cnt[i] > cap) {
+      fb[atomicAdd(fb_cnt, 1)] = qids[i];
+      cnt[i] = -1;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Tensor map of n x d BF16 rows (row stride d * 2 bytes, a multiple of 16),
+// boxes of 64 columns x box_rows rows, 128-byte swizzle; rows and columns
+// beyond the matrix read as zeros. Box x coordinates are multiples of 64
+// elements (128 bytes).
+static cudaError_t make_map(CUtensorMap* m, const void* base, int64_t n, int d, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    set_where("brute-force index: cuTensorMapEncodeTiled unavailable");
+    return cudaErrorNotSupported;
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)d, (cuuint64_t)n};
+  cuuint64_t gstride[1] = {(cuuint64_t)d * 2};
+  cuuint32_t box[2] = {(cuuint32_t)SC_KCH, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) set_where("brute-force index: tensor map");
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static size_t screen_smem() {
+  return 1024 + (size_t)SC_STAGES * SC_STAGE_BYTES + 2 * (size_t)SC_HALF * SC_EPI * 4 + 4 * (size_t)SC_N * 4;
+}
+
+template <int MODE, int PASS, int METRIC>
+static cudaError_t launch_screen_t(const CUtensorMap& ta, const CUtensorMap& tb, const ScreenArgs& a,
+                                   cudaStream_t st) {
+  auto kern = k_bf_screen<MODE, PASS, METRIC>;
+  const size_t smem = screen_smem();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    set_where("brute-force screen: shared-memory attribute");
+    return e;
+  }
+  const int64_t n_qt = (a.nq + SC_M - 1) / SC_M;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_qt, num_sms()));
+  kern<<<grid, SC_THREADS, smem, st>>>(ta, tb, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_screen(int mode, int pass, int metric, const CUtensorMap& ta, const CUtensorMap& tb,
+                                 const ScreenArgs& a, cudaStream_t st) {
+  if (a.nq <= 0) return cudaSuccess;
+  if (metric == MET_IP) {
+    if (mode == SCR_KNN)
+      return pass == SCR_KEEP ? launch_screen_t<SCR_KNN, SCR_KEEP, MET_IP>(ta, tb, a, st)
+                              : launch_screen_t<SCR_KNN, SCR_COLLECT, MET_IP>(ta, tb, a, st);
+    return pass == SCR_KEEP ? launch_screen_t<SCR_DEP, SCR_KEEP, MET_IP>(ta, tb, a, st)
+                            : launch_screen_t<SCR_DEP, SCR_COLLECT, MET_IP>(ta, tb, a, st);
+  }
+  if (mode == SCR_KNN)
+    return pass == SCR_KEEP ? launch_screen_t<SCR_KNN, SCR_KEEP, MET_L2>(ta, tb, a, st)
+                            : launch_screen_t<SCR_KNN, SCR_COLLECT, MET_L2>(ta, tb, a, st);
+  return pass == SCR_KEEP ? launch_screen_t<SCR_DEP, SCR_KEEP, MET_L2>(ta, tb, a, st)
+                          : launch_screen_t<SCR_DEP, SCR_COLLECT, MET_L2>(ta, tb, a, st);
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device scratch of the brute-force index (after the caller's own pieces).
+struct BfWs {
+  __nv_bfloat16* rows;   // n x d BF16 copy of the rows
+  __nv_bfloat16* qrows;  // up to n gathered query rows
+  float* nrm;            // n
+  float* nrm2;           // n
+  unsigned* maxbits;     // 1 (bits of the largest norm)
+  int32_t* cand;         // n x SC_KEEP (a collect batch: rows x SC_CAP)
+  int32_t* cnt;          // n
+  float* thr;            // n
+  int32_t* ovf;          // n overflowed rows
+  int32_t* ovf_ids;      // n
+  float* ovf_thr;        // n
+  int32_t* fb;           // n query ids for the exact SIMT kernels
+  int32_t* counters;     // [0] overflowed rows, [1] SIMT rows
+};
+
+size_t bf_ws_bytes(int64_t n, int d) {
+  return 2 * al256((size_t)n * d * 2) + al256((size_t)n * SC_KEEP * 4) + 9 * al256((size_t)n * 4) + 512;
+}
+
+static BfWs carve_bf(void* ws, int64_t n, int d) {
+  BfWs w;
+  uint8_t* p = (uint8_t*)ws;
+  auto take = [&](size_t bytes) {
+    uint8_t* q = p;
+    p += al256(bytes);
+    return q;
+  };
+  w.rows = (__nv_bfloat16*)take((size_t)n * d * 2);
+  w.qrows = (__nv_bfloat16*)take((size_t)n * d * 2);
+  w.cand = (int32_t*)take((size_t)n * SC_KEEP * 4);
+  w.nrm = (float*)take((size_t)n * 4);
+  w.nrm2 = (float*)take((size_t)n * 4);
+  w.cnt = (int32_t*)take((size_t)n * 4);
+  w.thr = (float*)take((size_t)n * 4);
+  w.ovf = (int32_t*)take((size_t)n * 4);
+  w.ovf_ids = (int32_t*)take((size_t)n * 4);
+  w.ovf_thr = (float*)take((size_t)n * 4);
+  w.fb = (int32_t*)take((size_t)n * 4);
+  w.maxbits = (unsigned*)take((size_t)n * 4);
+  w.counters = (int32_t*)take(256);
+  return w;
+}
+
+// Bounds of |approximate key - canonical key| (see ScreenArgs):
+//  - FP32 rows: BF16 rounding of both rows gives (2 u + u^2) |x| |y| with
+//    u = 2^-9, plus an allowance of 2^-12 |x| |y| for the FP32 accumulation
+//    of the tensor cores and of the canonical sum; IP adds 2^-22 for the
+//    rounding of 1 - s, L2 adds 2^-17 M^2 for the rounded squared norms and
+//    the canonical sum of squared differences;
+//  - uint8 rows: exact in BF16, every product and partial sum an integer
+//    below 2^24, so only an allowance of one unit per 16-column MMA step.
+static void eps_of(const DataView& fv, ScreenArgs* a) {
+  if (fv.dtype == DT_U8) {
+    a->eps_rel = 0.0f;
+    a->eps_abs = (float)((fv.d + 15) / 16);
+    a->eps_sq = 0.0f;
+  } else {
+    a->eps_rel = 1.0f / 256.0f + 1.0f / 4096.0f;
+    a->eps_abs = fv.metric == MET_IP ? 1.0f / 4194304.0f : 0.0f;
+    a->eps_sq = fv.metric == MET_L2 ? 1.0f / 131072.0f : 0.0f;
+  }
+}
+
+static cudaError_t prepare_rows(const DataView& fv, const BfWs& w, cudaStream_t st) {
+  const int64_t total = fv.n * (int64_t)fv.d;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
+  k_rows_to_bf16<<<blocks, 256, 0, st>>>(fv.X, fv.dtype, total, w.rows);
+  note_launch();
+  cudaError_t e = cudaMemsetAsync(w.maxbits, 0, 4, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.counters, 0, 256, st);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = (unsigned)std::min<int64_t>((fv.n * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  k_row_norms<<<nb, 256, 0, st>>>(fv.X, fv.dtype, fv.n, fv.d, fv.row_bytes, w.nrm, w.nrm2, w.maxbits);
+  note_launch();
+  return cudaGetLastError();
+}
+
+static ScreenArgs base_args(const DataView& fv, const BfWs& w, int* err) {
+  ScreenArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = fv.n;
+  a.kc = (fv.d + SC_KCH - 1) / SC_KCH;
+  a.pnorm2 = w.nrm2;
+  a.pnorm = w.nrm;
+  a.maxnorm = reinterpret_cast<const float*>(w.maxbits);
+  eps_of(fv, &a);
+  a.err = err;
+  return a;
+}
+
+static unsigned grid_for(int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 8192)); }
+
+static pecann_status read_count(const int32_t* d_cnt, int32_t* h, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(h, d_cnt, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e, "brute-force index: readback");
+}
+
+// Collect passes over the overflowed rows of a keep pass (m on the host), in
+// batches that fit the candidate buffer: each row's points under its
+// threshold are gathered (up to SC_CAP) and handed to `decide`, which runs
+// the exact re-rank on (query ids, candidates, counts, SC_CAP, rows); rows
+// beyond the capacity go to w.fb for the exact SIMT kernels.
+template <class DECIDE>
+static pecann_status collect_passes(int mode, const DataView& fv, const BfWs& w, const CUtensorMap& tp,
+                                    const int32_t* qids_of_rows, const float* rank_key, int k, int64_t m, int* err,
+                                    cudaStream_t st, DECIDE decide) {
+  const int64_t batch = std::max<int64_t>(1, (fv.n * SC_KEEP) / SC_CAP);
+  pecann_status s;
+  for (int64_t off = 0; off < m; off += batch) {
+    const int64_t mb = std::min(batch, m - off);
+    k_overflow_rows<<<grid_for(mb), 256, 0, st>>>(w.ovf, off, mb, qids_of_rows, w.thr, w.ovf_ids, w.ovf_thr);
+    note_launch();
+    k_gather_bf16<<<grid_for(mb * (fv.d / 8)), 256, 0, st>>>(w.rows, fv.d, w.ovf_ids, mb, w.qrows);
+    note_launch();
+    if ((s = cuda_status(cudaGetLastError(), "brute-force index: overflow rows"))) return s;
+    CUtensorMap tq;
+    if ((s = cuda_status(make_map(&tq, w.qrows, mb, fv.d, SC_M), "brute-force index"))) return s;
+    ScreenArgs a = base_args(fv, w, err);
+    a.nq = mb;
+    a.k = k;
+    a.qids = w.ovf_ids;
+    a.rank_key = rank_key;
+    a.in_thr = w.ovf_thr;
+    a.cap = SC_CAP;
+    a.out_ids = w.cand;
+    a.out_cnt = w.cnt;
+    if ((s = cuda_status(launch_screen(mode, SCR_COLLECT, fv.metric, tq, tp, a, st), "brute-force collect pass")))
+      return s;
+    k_collect_overflow<<<grid_for(mb), 256, 0, st>>>(w.cnt, mb, SC_CAP, w.ovf_ids, w.fb, w.counters + 1);
+    note_launch();
+    if ((s = cuda_status(cudaGetLastError(), "brute-force index: collect overflow"))) return s;
+    if ((s = decide(w.ovf_ids, w.cand, w.cnt, SC_CAP, mb))) return s;
+  }
+  return PECANN_OK;
+}
+
+pecann_status run_density_bf(const DataView& fv, const pecann_params* p, int32_t* knn_ids, float* knn_dist,
+                             float* rho, float* rkey, int32_t* fb_list, int32_t* fb_cnt, int* err, void* bws,
+                             int64_t* h_counts, cudaStream_t st) {
+  const BfWs w = carve_bf(bws, fv.n, fv.d);
+  pecann_status s;
+  if ((s = cuda_status(prepare_rows(fv, w, st), "brute-force index: rows"))) return s;
+  CUtensorMap tq, tp;
+  if ((s = cuda_status(make_map(&tq, w.rows, fv.n, fv.d, SC_M), "brute-force index"))) return s;
+  if ((s = cuda_status(make_map(&tp, w.rows, fv.n, fv.d, SC_N), "brute-force index"))) return s;
+  ScreenArgs a = base_args(fv, w, err);
+  a.nq = fv.n;
+  a.k = p->k;
+  a.out_ids = w.cand;
+  a.out_cnt = w.cnt;
+  a.out_thr = w.thr;
+  a.ovf_list = w.ovf;
+  a.ovf_cnt = w.counters + 0;
+  if ((s = cuda_status(launch_screen(SCR_KNN, SCR_KEEP, fv.metric, tq, tp, a, st), "brute-force screen"))) return s;
+  // exact decision for the complete rows (overflowed rows carry -1: skipped)
+  cudaError_t e = launch_rerank_knn(fv, nullptr, fv.n, w.cand, w.cnt, SC_KEEP, p->k, knn_ids, knn_dist, rho, rkey,
+                                    p->density, fb_list, fb_cnt, st);
+  if ((s = cuda_status(e, "brute-force index: exact k-NN"))) return s;
+  int32_t m = 0;
+  if ((s = read_count(w.counters + 0, &m, st))) return s;
+  auto decide = [&](const int32_t* ids, const int32_t* cand, const int32_t* cnt, int K, int64_t rows) {
+    return cuda_status(launch_rerank_knn(fv, ids, rows, cand, cnt, K, p->k, knn_ids, knn_dist, rho, rkey,
+                                         p->density, fb_list, fb_cnt, st),
+                       "brute-force index: exact k-NN");
+  };
+  if ((s = collect_passes(SCR_KNN, fv, w, tp, nullptr, nullptr, p->k, m, err, st, decide))) return s;
+  // rows beyond the collect capacity join the fallback list of the caller
+  int32_t m2 = 0;
+  if ((s = read_count(w.counters + 1, &m2, st))) return s;
+  if (m2 > 0) {
+    int32_t base = 0;
+    if ((s = read_count(fb_cnt, &base, st))) return s;
+    e = cudaMemcpyAsync(fb_list + base, w.fb, (size_t)m2 * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+      const int32_t total = base + m2;
+      e = cudaMemcpyAsync(fb_cnt, &total, 4, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if ((s = cuda_status(e, "brute-force index: fallback list"))) return s;
+  }
+  if (h_counts) {
+    h_counts[0] = m;
+    h_counts[1] = m2;
+  }
+  return PECANN_OK;
+}
+
+pecann_status run_dep_bf(const DataView& fv, const float* rank_key, const int32_t* U, int64_t nu, int32_t* lam,
+                         float* delta, int* err, void* bws, int64_t* h_counts, cudaStream_t st) {
+  if (nu <= 0) return PECANN_OK;
+  const BfWs w = carve_bf(bws, fv.n, fv.d);
+  pecann_status s;
+  if ((s = cuda_status(prepare_rows(fv, w, st), "brute-force index: rows"))) return s;
+  k_gather_bf16<<<grid_for(nu * (fv.d / 8)), 256, 0, st>>>(w.rows, fv.d, U, nu, w.qrows);
+  note_launch();
+  if ((s = cuda_status(cudaGetLastError(), "brute-force index: gather"))) return s;
+  CUtensorMap tq, tp;
+  if ((s = cuda_status(make_map(&tq, w.qrows, nu, fv.d, SC_M), "brute-force index"))) return s;
+  if ((s = cuda_status(make_map(&tp, w.rows, fv.n, fv.d, SC_N), "brute-force index"))) return s;
+  ScreenArgs a = base_args(fv, w, err);
+  a.nq = nu;
+  a.qids = U;
+  a.rank_key = rank_key;
+  a.out_ids = w.cand;
+  a.out_cnt = w.cnt;
+  a.out_thr = w.thr;
+  a.ovf_list = w.ovf;
+  a.ovf_cnt = w.counters + 0;
+  if ((s = cuda_status(launch_screen(SCR_DEP, SCR_KEEP, fv.metric, tq, tp, a, st), "brute-force screen"))) return s;
+  cudaError_t e = launch_rerank_dep(fv, U, nu, w.cand, w.cnt, SC_KEEP, lam, delta, st);
+  if ((s = cuda_status(e, "brute-force index: exact dependent points"))) return s;
+  int32_t m = 0;
+  if ((s = read_count(w.counters + 0, &m, st))) return s;
+  auto decide = [&](const int32_t* ids, const int32_t* cand, const int32_t* cnt, int K, int64_t rows) {
+    return cuda_status(launch_rerank_dep(fv, ids, rows, cand, cnt, K, lam, delta, st),
+                       "brute-force index: exact dependent points");
+  };
+  if ((s = collect_passes(SCR_DEP, fv, w, tp, U, rank_key, 0, m, err, st, decide))) return s;
+  int32_t m2 = 0;
+  if ((s = read_count(w.counters + 1, &m2, st))) return s;
+  if (m2 > 0) {
+    // the exact SIMT tail; its per-query keys take the candidate buffer
+    e = launch_dep_bruteforce(fv, w.fb, m2, rank_key, reinterpret_cast<unsigned long long*>(w.cand), lam, delta, st);
+    if ((s = cuda_status(e, "brute-force index: exact tail"))) return s;
+  }
+  if (h_counts) {
+    h_counts[0] = m;
+    h_counts[1] = m2;
+  }
+  return PECANN_OK;
+}
+
+}  // namespace pecann

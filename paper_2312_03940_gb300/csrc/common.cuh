@@ -34,7 +34,8 @@ enum : int {
   ERR_NONE = 0,
   ERR_BAD_ID = 1,        // a graph entry or query id outside [0, n)
   ERR_NO_PROGRESS = 2,   // a search expanded more points than exist
-  ERR_CAPACITY = 3       // a staging buffer was too small
+  ERR_CAPACITY = 3,      // a staging buffer was too small
+  ERR_TIMEOUT = 4        // a pipeline wait of the tensor-core screen ran past its limit
 };
 
 __device__ __forceinline__ void set_error(int* err, int code) {

@@ -117,15 +117,18 @@ cudaError_t launch_dep_bruteforce(const DataView& dv, const int32_t* d_list, int
                                   const float* rank_key, unsigned long long* best, int32_t* lam,
                                   float* delta, cudaStream_t st);
 
-// Exact FP32 re-rank of candidates found on reduced-precision rows.
-// k-NN: for each point q (0..n-1), the cnt[q] <= K ids cand[q*K ..] are
-// re-scored on the FP32 rows; the k closest (by exact (dis, id)) and the
-// density are written; points with cnt[q] < k are appended to fb_list.
-cudaError_t launch_rerank_knn(const DataView& f32, const int32_t* cand, const int32_t* cnt, int K, int k,
-                              int32_t* knn_ids, float* knn_dist, float* rho, float* rkey, int density_fn,
-                              int32_t* fb_list, int32_t* fb_cnt, cudaStream_t st);
-// Dependent rounds: for each listed query u, the exact closest of its
-// cnt[u] <= K candidates cand[u*K ..] (all ranked above it) becomes lambda.
+// Exact FP32 re-rank of candidates found on reduced-precision rows or by
+// the brute-force screen. k-NN: for each row u (0..rows), the cnt[u] <= K
+// ids cand[u*K ..] of query q = list[u] (list NULL: q = u) are re-scored on
+// the FP32 (or uint8) rows; the k closest (by exact (dis, id)) and the
+// density are written at q; queries with 0 <= cnt[u] < k are appended to
+// fb_list; rows with cnt[u] < 0 are skipped.
+cudaError_t launch_rerank_knn(const DataView& f32, const int32_t* list, int64_t rows, const int32_t* cand,
+                              const int32_t* cnt, int K, int k, int32_t* knn_ids, float* knn_dist, float* rho,
+                              float* rkey, int density_fn, int32_t* fb_list, int32_t* fb_cnt, cudaStream_t st);
+// Dependent points: for each listed query u, the exact closest of its
+// cnt[u] <= K candidates cand[u*K ..] (all ranked above it) becomes lambda;
+// rows with cnt[u] <= 0 are skipped.
 cudaError_t launch_rerank_dep(const DataView& f32, const int32_t* list, int64_t m, const int32_t* cand,
                               const int32_t* cnt, int K, int32_t* lam, float* delta, cudaStream_t st);
 
@@ -135,6 +138,7 @@ cudaError_t launch_rerank_dep(const DataView& f32, const int32_t* list, int64_t 
 // rows: the same view for FP32 / U8 data, data_f32 for BF16 / FP8.
 pecann_status check_dataset(const pecann_dataset* ds, DataView* dv, DataView* f32 = nullptr);
 pecann_status check_params(const pecann_params* p, int64_t n);
+pecann_status check_index(const DataView& dv, const pecann_params* p);
 pecann_status check_density_args(const DataView& dv, const int32_t* d_graph, const pecann_params* p,
                                  const int32_t* d_knn_ids, const float* d_knn_dist, const float* d_density,
                                  const float* d_rank_key);
@@ -156,10 +160,24 @@ struct DensityScratch {
   int32_t* rr_ids = nullptr;
   float* rr_dis = nullptr;
   int32_t* rr_cnt = nullptr;
+  void* bf_ws = nullptr;          // brute-force index: its scratch (bf_ws_bytes)
+  int64_t* bf_counts = nullptr;   // brute-force index: host, 2 entries (see run_density_bf)
 };
 pecann_status run_density(const DataView& dv, const DataView& fv, const int32_t* d_graph, const pecann_params* p,
                           int32_t* d_knn_ids, float* d_knn_dist, float* d_density, float* d_rank_key,
                           const DensityScratch& sc, cudaStream_t st);
+
+// The brute-force index on the tensor cores (bf_screen.cu). bws is a device
+// scratch of bf_ws_bytes(n, d) bytes, 256-byte aligned. fv: the FP32 (or
+// uint8) rows. h_counts (host, 2 entries, may be NULL): rows that took the
+// collect pass, rows left to the exact SIMT kernels.
+size_t bf_ws_bytes(int64_t n, int d);
+pecann_status run_density_bf(const DataView& fv, const pecann_params* p, int32_t* knn_ids, float* knn_dist,
+                             float* rho, float* rkey, int32_t* fb_list, int32_t* fb_cnt, int* err, void* bws,
+                             int64_t* h_counts, cudaStream_t st);
+// DPBruteForce over all points for the nu listed (unfinished) points U.
+pecann_status run_dep_bf(const DataView& fv, const float* rank_key, const int32_t* U, int64_t nu, int32_t* lam,
+                         float* delta, int* err, void* bws, int64_t* h_counts, cudaStream_t st);
 
 int num_sms();
 // Counts the kernels the library launches (reported by pecann_kernel_launches).

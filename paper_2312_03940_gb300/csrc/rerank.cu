@@ -12,7 +12,7 @@ struct RerankArgs {
   SearchArgs a;          // FP32 rows, metric, k, outputs, density_fn
   const int32_t* cand;   // candidates, K per row
   const int32_t* cnt;    // valid candidates per row
-  const int32_t* list;   // dep: query ids of the rows (NULL: row = query id)
+  const int32_t* list;   // query ids of the rows (NULL: row = query id)
   int64_t rows;
   int K;
 };
@@ -28,8 +28,10 @@ __global__ void __launch_bounds__(128) k_rerank_knn(RerankArgs r) {
   WarpSmem w = carve(smem + (size_t)wib * a.warp_bytes, a);
   const int gl = lane % W;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; q < r.rows; q += nw) {
-    const int c = min(r.cnt[q], r.K);
+  for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; u < r.rows; u += nw) {
+    const int c = min(r.cnt[u], r.K);
+    if (c < 0) continue;  // handled elsewhere (a later pass or the exact SIMT kernels)
+    const int64_t q = r.list ? (int64_t)r.list[u] : u;
     if (c < a.k) {
       if (lane == 0) a.fb_list[atomicAdd(a.fb_cnt, 1)] = (int32_t)q;
       continue;
@@ -39,7 +41,7 @@ __global__ void __launch_bounds__(128) k_rerank_knn(RerankArgs r) {
     int nb = 0, cursor = 0;
     for (int c0 = 0; c0 < c; c0 += a.stage) {
       const int nc = min(a.stage, c - c0);
-      for (int i = lane; i < nc; i += 32) w.cids[i] = r.cand[q * r.K + c0 + i];
+      for (int i = lane; i < nc; i += 32) w.cids[i] = r.cand[u * r.K + c0 + i];
       __syncwarp();
       eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
       merge_cands(w, nb, a.k, nc, cursor, lane);
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(128) k_rerank_dep(RerankArgs r) {
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; u < r.rows; u += nw) {
     const int c = min(r.cnt[u], r.K);
-    if (c == 0) continue;
+    if (c <= 0) continue;  // none ranked above, or handled elsewhere (-1)
     const int32_t q = r.list[u];
     uint4 qv[CPL];
     load_row<W, CPL, false>(a.X + (int64_t)q * a.row_bytes, gl, a.C, qv);
@@ -121,9 +123,10 @@ static void fill_common(RerankArgs& r, const DataView& f32, int beam) {
   a.warp_bytes = search_warp_bytes(beam, 0, a.stage, 0, false);
 }
 
-cudaError_t launch_rerank_knn(const DataView& f32, const int32_t* cand, const int32_t* cnt, int K, int k,
-                              int32_t* knn_ids, float* knn_dist, float* rho, float* rkey, int density_fn,
-                              int32_t* fb_list, int32_t* fb_cnt, cudaStream_t st) {
+cudaError_t launch_rerank_knn(const DataView& f32, const int32_t* list, int64_t rows, const int32_t* cand,
+                              const int32_t* cnt, int K, int k, int32_t* knn_ids, float* knn_dist, float* rho,
+                              float* rkey, int density_fn, int32_t* fb_list, int32_t* fb_cnt, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
   RerankArgs r;
   fill_common(r, f32, k);
   r.a.k = k;
@@ -136,7 +139,8 @@ cudaError_t launch_rerank_knn(const DataView& f32, const int32_t* cand, const in
   r.a.fb_cnt = fb_cnt;
   r.cand = cand;
   r.cnt = cnt;
-  r.rows = f32.n;
+  r.list = list;
+  r.rows = rows;
   r.K = K;
   return dispatch_layout(f32, [&](auto dt, auto met, auto wv, auto cpl) -> cudaError_t {
     return launch_rr(k_rerank_knn<decltype(dt)::value, decltype(met)::value, decltype(wv)::value,

@@ -20,6 +20,7 @@ F32, U8, BF16, FP8E4M3 = 0, 1, 2, 3
 L2, IP = 0, 1
 DENS_KTH, DENS_EXPSUM, DENS_SUMEXP, DENS_SUM = 0, 1, 2, 3
 CENTER_THRESHOLD, CENTER_PRODUCT, CENTER_LOCAL = 0, 1, 2
+INDEX_GRAPH, INDEX_BRUTE_FORCE = 0, 1
 
 _DTYPES = {torch.float32: F32, torch.uint8: U8, torch.bfloat16: BF16}
 if hasattr(torch, "float8_e4m3fn"):
@@ -35,7 +36,7 @@ class PecannParams(ctypes.Structure):
                 ("normalize_density", ctypes.c_int32), ("center", ctypes.c_int32), ("rho_min", ctypes.c_float),
                 ("delta_min", ctypes.c_float), ("n_clusters", ctypes.c_int32), ("hash_slots", ctypes.c_int32),
                 ("collect_work", ctypes.c_int32), ("build_passes", ctypes.c_int32), ("rerank_k", ctypes.c_int32), ("block_warps", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32),
+                ("index", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 
@@ -229,8 +230,10 @@ def pecann_build_graph(ds: Dataset, p: PecannParams, order: torch.Tensor | None 
 
 def pecann_density(ds: Dataset, graph: torch.Tensor, p: PecannParams, ws: torch.Tensor | None = None,
                    stream=None, out: dict | None = None):
-    """k-NN and density of every point. Returns dict knn_ids, knn_dist, density, rank_key."""
-    _cuda(graph, "graph", torch.int32)
+    """k-NN and density of every point. Returns dict knn_ids, knn_dist, density, rank_key.
+    graph may be None with p.index = INDEX_BRUTE_FORCE."""
+    if graph is not None:
+        _cuda(graph, "graph", torch.int32)
     ws = ws if ws is not None else workspace(ds, p)
     dev = ds.X.device
     if out is None:
@@ -266,8 +269,10 @@ def pecann_density_noalloc(ds: Dataset, graph: torch.Tensor, p: PecannParams, st
 def pecann_dependent_points(ds: Dataset, graph: torch.Tensor, p: PecannParams, rank_key: torch.Tensor,
                             knn_ids: torch.Tensor, knn_dist: torch.Tensor, ws: torch.Tensor | None = None,
                             stream=None, out: dict | None = None):
-    """Algorithm 3. Returns dict dep, dep_dist, stats (list of 64 ints)."""
-    _cuda(graph, "graph", torch.int32)
+    """Algorithm 3. Returns dict dep, dep_dist, stats (list of 64 ints).
+    graph may be None with p.index = INDEX_BRUTE_FORCE."""
+    if graph is not None:
+        _cuda(graph, "graph", torch.int32)
     _cuda(rank_key, "rank_key", torch.float32)
     _cuda(knn_ids, "knn_ids", torch.int32)
     _cuda(knn_dist, "knn_dist", torch.float32)

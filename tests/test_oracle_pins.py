@@ -378,6 +378,34 @@ def test_ari_matches_sklearn():
         assert abs(exact.ari(a, b) - sk.adjusted_rand_score(a, b)) < 1e-12
 
 
+def test_bruteforce_index_equals_exact_dpc():
+    """The brute-force index (Sec. 5.1: no index, exact k-NN by scanning every
+    point) in the oracle: its k-NN lists equal the FP64 exact k-NN, and
+    Algorithm 3 run literally with that exact FindKnn (doubling rounds, then
+    the tail) gives Definition 2.1's dependent points for the same keys. The
+    Gaussian data leaves no FP32 near-ties among the compared distances."""
+    X, _ = _mixture(3000, 32, 6, np.random.default_rng(3))
+    P = oracle.Points(X)
+    o = oracle.knn_density(P, None, L=0, k=8)
+    ei, ed = exact.exact_knn(X, 8)
+    assert (o["ids"] == ei).all()
+    assert np.allclose(o["dist"], ed, rtol=1e-6, atol=0)
+    assert (o["fallback"] == 0).all()
+    d = oracle.dependent_points(P, None, o["key"], o["ids"], Ld=16, threshold=10)
+    assert d["rounds"] >= 1 and d["unfinished_round0"] > d["tail"]  # the exact rounds did work
+    lam, delta = exact.exact_dependent(X, o["key"].astype(np.float64))
+    assert (d["lam"] == lam).all()
+    ok = lam >= 0
+    assert np.allclose(d["delta"][ok], delta[ok], rtol=1e-6, atol=0)
+    # inner product on unit-norm rows (isotropic directions: no near-ties)
+    Xs = np.random.default_rng(4).standard_normal((2000, 32)).astype(np.float32)
+    Xs /= np.linalg.norm(Xs, axis=1, keepdims=True)
+    Ps = oracle.Points(Xs, metric=oracle.IP)
+    o2 = oracle.knn_density(Ps, None, L=0, k=5)
+    ei2, _ = exact.exact_knn(Xs, 5, metric=exact.IP)
+    assert (o2["ids"] == ei2).all()
+
+
 def test_ari_closed_form_at_scale():
     """Halves against quarters nested in them, n = 4m points. By hand: S_ij =
     S_b = 2m(m-1), S_a = 2m(2m-1), T = 2m(4m-1); E = S_a S_b / T =
