@@ -1,15 +1,26 @@
 #!/usr/bin/env python3
 """DPC points/sec on one GB300: density + dependent points (+ clusters).
 
-Workload: n = 1,000,000 x d = 128 uint8 Gaussian mixture (100 components,
-Zipf(1.1) weights, per-component sigma in [5, 20], 5% uniform noise points),
-Vamana R = 64, L = 128, alpha = 1.2, k = 10, product center with 100
-clusters. A step is one pass of the path over the whole point set on the
-graph the GPU built beforehand: k-NN + density, dependent points (round 0,
-doubling rounds, brute-force tail) and the cluster cut. The graph build is
-timed separately and reported as build_s.
+Headline workload: n = 1,280,000 unit-norm rows of d = 1024 (1,000 vMF-like
+clusters, concentration log-uniform in [20, 200], log-normal sizes; inner
+product), k = 16, product center with 1,000 clusters, on the brute-force index
+(Sec. 5.1: exact k-NN; tensor-core screen, exact FP32 decision). On this data
+the Vamana graph (R = 64) stays far below the 0.95 k-NN recall the metric is
+quoted at (0.64 at beam 200, 0.69 at beam 1,600), so the exact index is the
+configuration that meets it; the graph path is reported beside it.
+
+A step is one pass of the path over the whole point set: k-NN + density,
+dependent points, the cluster cut. The same JSON line carries, under
+"variants", report lines measured in the same run:
+  * the 1.28M x 1024 set on a Vamana graph (R 64, beam 200) with FP32, BF16
+    and FP8-e4m3 traversal and exact FP32 re-rank, recall and ARI judged
+    against the exact index at full n;
+  * n = 1,000,000 x d = 128 uint8 (100 Zipf-weighted Gaussians + 5% noise) on
+    its Vamana graph (R 64, beam 128, k 10) and on the exact index.
+Graph builds are timed separately (build_s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload vmf1024|u8-1m|batched64|sphere384] [--quick]
 
 Prints one JSON line (rank 0). For N > 1 (torchrun) every rank runs its own
 replica of the workload on its GPU; value = all points processed / the max
@@ -30,17 +41,20 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# The k-NN / dependent searches use beam L = 128. The build (outside the
-# metric) uses two passes, beam 256 and 8192 random start points: the paper
-# leaves these open, and they give >= 0.95 k-NN recall on this data.
-WORKLOAD = dict(n=1_000_000, d=128, components=100, R=64, L=128, alpha=1.2, k=10, n_clusters=100,
-                L_build=256, n_start=8192, build_passes=2)
-WORKLOAD_NAME = ("u8-gaussian-mixture n=1,000,000 d=128 (100 components, Zipf 1.1 weights, sigma U[5,20], "
-                 "5% uniform noise); Vamana R=64 L=128 alpha=1.2 (build: 2 passes, L=256, 8192 start points); "
-                 "kth density k=10; product center 100")
 METRIC = "DPC points/sec (density + dependent-point search) at >=0.95 recall; % HBM peak"
 UNIT = "points/s"
-SUBSET_N = 10_000  # oracle sample: the same generator at 10k points
+
+VMF = dict(n=1_280_000, d=1024, components=1000, k=16, n_clusters=1000, R=64, L=200, L_build=400, alpha=1.2,
+           build_passes=2, n_start=10485)
+VMF_NAME = ("vmf-like unit-norm n=1,280,000 d=1024 inner product (1,000 clusters, kappa log-uniform [20,200], "
+            "log-normal sizes); kth density k=16; product center 1000")
+U8 = dict(n=1_000_000, d=128, components=100, R=64, L=128, alpha=1.2, k=10, n_clusters=100, L_build=256,
+          n_start=8192, build_passes=2)
+U8_NAME = ("u8-gaussian-mixture n=1,000,000 d=128 (100 components, Zipf 1.1 weights, sigma U[5,20], "
+           "5% uniform noise); kth density k=10; product center 100")
+CPU_SAMPLE = 16       # points per oracle timing sample (brute-force index on the full rows)
+CPU_SAMPLE_GRAPH = 256  # points per oracle timing sample (beam search on the same graph)
+RECALL_QUERIES = 200  # FP64 exact k-NN of sampled points (CPU)
 
 
 def parse():
@@ -49,11 +63,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (profiling runs use fewer)")
-    ap.add_argument("--quick", action="store_true", help="skip recall, e2e and the CPU baseline")
-    ap.add_argument("--subset", type=int, default=SUBSET_N)
-    ap.add_argument("--workload", default="u8-1m", choices=["u8-1m", "batched64", "sphere384", "vmf1024"],
-                    help="u8-1m: the benchmark line; the others print extra report lines")
+    ap.add_argument("--n", type=int, default=0, help="points (profiling runs use fewer; 0 = the workload's)")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: no variants, recall, e2e or CPU baseline")
+    ap.add_argument("--variant-steps", type=int, default=2, help="timed steps of each report line")
+    ap.add_argument("--workload", default="vmf1024", choices=["vmf1024", "u8-1m", "batched64", "sphere384"],
+                    help="vmf1024: the benchmark line (with its variants); u8-1m: the uint8 graph line alone")
     return ap.parse_args()
 
 
@@ -62,7 +77,7 @@ def peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 # ---------------------------------------------------------------- clocks
@@ -167,34 +182,188 @@ def profiled_traffic(kernel_tag: str):
         return None
 
 
-def oracle_subset_run(n_sub: int, threads: int, steps: int = 1, warmup: int = 0):
-    """The CPU oracle's whole path (k-NN + density, dependent points, clusters)
-    on an n_sub-point sample drawn from the same generator, on a graph the
-    oracle builds itself (untimed). Returns points/s over the timed steps."""
+# ---------------------------------------------------------------- workloads
+
+def vmf_data(n):
+    from paper_2312_03940_gb300 import synth
+
+    return synth.vmf_like(n=n, d=VMF["d"], components=VMF["components"])
+
+
+def u8_data(n):
+    from paper_2312_03940_gb300 import synth
+
+    return synth.u8_mixture(n=n, d=U8["d"], components=U8["components"])
+
+
+def cpu_knn_rate(X, metric, G, L, k, m, threads, steps=1, seed=11):
+    """The oracle as it stands, timed on the host cores: k-NN + density of m
+    sampled points of the same rows (G None: the brute-force index; else
+    Algorithm 1 on the same graph). Returns (points/s, seconds, sample text)."""
     import oracle
     from paper_2312_03940_gb300 import synth
 
-    X, _ = synth.u8_mixture(n=n_sub, d=WORKLOAD["d"], components=WORKLOAD["components"])
-    P = oracle.Points(X)
-    # start points in the same proportion to n as on the full workload
-    n_start = max(16, WORKLOAD["n_start"] * n_sub // WORKLOAD["n"])
-    G = oracle.build_graph(P, R=WORKLOAD["R"], L=WORKLOAD["L_build"], alpha=WORKLOAD["alpha"],
-                           perm=synth.insertion_order(n_sub), n_start=n_start, threads=threads,
-                           passes=WORKLOAD["build_passes"])
+    P = oracle.Points(X, metric=metric)
+    dt = 0.0
+    for s in range(steps):
+        rows = synth.sample_ids(len(X), m, seed=seed + s)
+        t0 = time.perf_counter()
+        oracle.knn_density_rows(P, G, rows, L=L, k=k, threads=threads)
+        dt += time.perf_counter() - t0
+    return m * steps / dt, dt
 
-    def one():
-        r = oracle.knn_density(P, G, L=WORKLOAD["L"], k=WORKLOAD["k"], threads=threads)
-        d = oracle.dependent_points(P, G, r["key"], r["ids"], Ld=WORKLOAD["L"], threshold=300, threads=threads)
-        oracle.cluster(r["rho"], d["lam"], d["delta"], center=oracle.CENTER_PRODUCT,
-                       n_clusters=WORKLOAD["n_clusters"])
+
+def exact_recall(X, metric, knn_dist, k, m=RECALL_QUERIES, seed=12):
+    """Tie-aware k-NN recall of sampled points against the FP64 exact k-NN."""
+    from oracle import exact
+    from paper_2312_03940_gb300 import synth
+
+    qs = synth.sample_ids(len(X), m, seed=seed)
+    _, ex = exact.exact_knn_queries(X, qs, k, metric=exact.IP if metric == 1 else exact.L2)
+    return exact.knn_recall(knn_dist[qs], ex)
+
+
+def full_recall(got_dist, exact_dist):
+    """Tie-aware recall over every point, against exact k-NN distances."""
+    kth = exact_dist[:, -1:]
+    return float((got_dist <= kth * (1.0 + 1e-5) + 1e-30).mean())
+
+
+def timed(step, warmup, steps, stream):
+    """W untimed steps, then K steps between CUDA events on `stream`; also the
+    per-step density-call events that step() records. Returns seconds."""
+    import torch
 
     for _ in range(warmup):
-        one()
+        step(None)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dens = []
+    e0.record(stream)
+    for _ in range(steps):
+        step(dens)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dens_ms = [a.elapsed_time(b) for a, b in dens]
+    return e0.elapsed_time(e1) / 1e3, (float(np.mean(dens_ms)) if dens_ms else None)
+
+
+class Path:
+    """One DPC configuration on one dataset: the calls of a step, reusing
+    outputs and workspace."""
+
+    def __init__(self, ds, G, p, dev):
+        import torch
+
+        from paper_2312_03940_gb300 import pecann as pc
+
+        self.pc, self.ds, self.G, self.p = pc, ds, G, p
+        n = ds.n
+        self.ws = pc.workspace(ds, p)
+        self.cws = torch.empty(8 * n + (1 << 20), dtype=torch.uint8, device=dev)
+        self.dens = dict(knn_ids=torch.empty((n, p.k), dtype=torch.int32, device=dev),
+                         knn_dist=torch.empty((n, p.k), dtype=torch.float32, device=dev),
+                         density=torch.empty(n, dtype=torch.float32, device=dev),
+                         rank_key=torch.empty(n, dtype=torch.float32, device=dev))
+        self.dep = dict(dep=torch.empty(n, dtype=torch.int32, device=dev),
+                        dep_dist=torch.empty(n, dtype=torch.float32, device=dev))
+        self.labels = torch.empty(n, dtype=torch.int32, device=dev)
+        self.stats = None
+
+    def step(self, dens_events=None, ds=None, G=None):
+        import torch
+
+        pc = self.pc
+        ds = ds or self.ds
+        G = self.G if G is None else G
+        if dens_events is not None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+        pc.pecann_density(ds, G, self.p, ws=self.ws, out=self.dens)
+        if dens_events is not None:
+            b.record()
+            dens_events.append((a, b))
+        r = pc.pecann_dependent_points(ds, G, self.p, self.dens["rank_key"], self.dens["knn_ids"],
+                                       self.dens["knn_dist"], ws=self.ws, out=self.dep)
+        self.stats = r["stats"]
+        pc.pecann_cluster(self.dens["density"], self.dep["dep"], self.dep["dep_dist"], self.p, ws=self.cws,
+                          count=False, labels=self.labels)
+
+    def screen_counts(self):
+        """Brute-force index: points of the last call that took the collect
+        pass and that the exact SIMT kernels took."""
+        return [int(x) for x in self.ws[24:32].cpu().view(__import__("torch").int32).tolist()]
+
+
+def e2e_rate(path, X_host, G_host, steps):
+    """The same metric end to end through the public calls: every step copies
+    the rows (and graph) in from pinned host memory and reads rho, dependent
+    points, their distances and the labels back."""
+    import torch
+
+    from paper_2312_03940_gb300 import pecann as pc
+
+    dev = path.ds.X.device
+    Xh = torch.from_numpy(X_host).pin_memory()
+    Xd = torch.empty_like(path.ds.X)
+    ds = pc.Dataset(Xd, metric=path.ds.metric)
+    Gh = G_host.pin_memory() if G_host is not None else None
+    Gd = torch.empty_like(path.G) if G_host is not None else None
+    n = path.ds.n
+    outs = [torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory(),
+            torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory()]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        one()
-    dt = time.perf_counter() - t0
-    return n_sub * steps / dt, dt
+        Xd.copy_(Xh, non_blocking=True)
+        if Gd is not None:
+            Gd.copy_(Gh, non_blocking=True)
+        path.step(None, ds=ds, G=Gd)
+        for h, d in zip(outs, [path.dens["density"], path.dep["dep"], path.dep["dep_dist"], path.labels]):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    h2d = int(Xh.numel() * Xh.element_size() + (Gh.numel() * 4 if Gh is not None else 0))
+    return {"value": n / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(16 * n)}
+
+
+_COUNTS = {}
+
+
+def graph_roofline(X, metric, Gh, p, row_bytes, dens_s, n, kernel, peak_key="hbm_gbs", traffic_tag=None):
+    """Algorithmic bytes of the k-NN beam search per launch: E_q out-lists of
+    4R bytes, (C_q + 1) rows, 8k bytes of output and 8 bytes of density per
+    query, with E_q and C_q counted by the oracle on 1,000 sampled queries of
+    the same graph (its trajectory is the GPU's FP32 trajectory)."""
+    import oracle
+    from paper_2312_03940_gb300 import synth
+
+    key = (id(Gh), p.L_search)
+    if key not in _COUNTS:
+        P = oracle.Points(X, metric=metric)
+        _COUNTS[key] = oracle.search_counts(P, Gh, synth.sample_ids(n, 1000, seed=99), L=p.L_search)
+    e_q, c_q = _COUNTS[key]
+    bytes_q = e_q.mean() * 4 * p.R + (c_q.mean() + 1) * row_bytes + 8 * p.k + 8
+    alg = bytes_q * n
+    pk, src = peaks()
+    ach = alg / dens_s / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": pk[peak_key], "peak_source": src,
+            "unit": "GB/s", "frac": ach / pk[peak_key], "traffic": profiled_traffic(traffic_tag) if traffic_tag else None,
+            "algorithmic_bytes_per_launch": alg, "E_q": float(e_q.mean()), "C_q": float(c_q.mean())}
+
+
+def screen_roofline(n, d, collect_rows, dens_s, traffic_tag=None):
+    """Algorithmic tensor FLOPs of the brute-force screen per density call:
+    2 n^2 d for the keep pass plus 2 m n d for the m points of the collect
+    pass, over the whole call (screen, collect, exact re-rank)."""
+    pk, src = peaks()
+    flops = 2.0 * n * n * d + 2.0 * collect_rows * n * d
+    ach = flops / dens_s / 1e12
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    return {"kernel": "k_bf_screen (BF16 tcgen05 screen of the k-NN pass, whole density call)", "bound": "tensor",
+            "achieved": ach, "peak": peak, "peak_source": src + " (bf16, sustained)", "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": profiled_traffic(traffic_tag) if traffic_tag else None,
+            "algorithmic_flops_per_launch": flops, "collect_rows": int(collect_rows)}
 
 
 # ---------------------------------------------------------------- reference arm (the CPU oracle)
@@ -207,14 +376,19 @@ def run_reference(args):
 
     oracle.build()
     threads = oracle.default_threads()
-    n_sub = args.subset
-    rate, dt = oracle_subset_run(n_sub, threads, steps=args.steps, warmup=args.warmup)
-    sample = (f"oracle k-NN+density, dependent points and clusters on a {n_sub}-point sample of the same "
-              f"generator (its own graph, built untimed), {args.steps} steps")
+    n = args.n or VMF["n"]
+    X, _ = vmf_data(n)
+    for _ in range(args.warmup):
+        cpu_knn_rate(X, 1, None, 0, VMF["k"], CPU_SAMPLE, threads, seed=500)
+    rate, dt = cpu_knn_rate(X, 1, None, 0, VMF["k"], CPU_SAMPLE, threads, steps=args.steps)
+    sample = (f"oracle brute-force index (exact k-NN + kth density, canonical FP32) of {CPU_SAMPLE} sampled points "
+              f"per step over all {n:,} rows of the same workload, {args.steps} steps; the dependent step is not in "
+              f"the sample (so the CPU rate is an upper bound)")
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "oracle_sample_points": n_sub},
+           "config": {"workload": VMF_NAME if n == VMF["n"] else VMF_NAME.replace("1,280,000", f"{n:,}"),
+                      "index": "brute force (exact)", "oracle_points_per_step": CPU_SAMPLE},
            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -245,162 +419,213 @@ def run_ours(args):
     if dist:
         dist.barrier()
     pc.load_library()
+    stream = torch.cuda.current_stream()
 
     def barrier():
         if dist:
             dist.barrier()
 
-    n = args.n
-    X, gt = synth.u8_mixture(n=n, d=WORKLOAD["d"], components=WORKLOAD["components"])
-    order = synth.insertion_order(n)
-    p = pc.params(k=WORKLOAD["k"], R=WORKLOAD["R"], L_build=WORKLOAD["L_build"], L_search=WORKLOAD["L"],
-                  L_dep=WORKLOAD["L"], alpha=WORKLOAD["alpha"], n_start=min(n, WORKLOAD["n_start"]),
-                  build_passes=WORKLOAD["build_passes"], center=pc.CENTER_PRODUCT,
-                  n_clusters=WORKLOAD["n_clusters"])
+    # ---- the headline: 1.28M x 1024 on the brute-force index
+    n = args.n or VMF["n"]
+    X, gt = vmf_data(n)
     Xd = torch.from_numpy(X).to(dev)
-    ds = pc.Dataset(Xd)
-    ws = pc.workspace(ds, p)
-    stream = torch.cuda.current_stream()
-
-    # ---- graph build (not part of the metric)
+    ds = pc.Dataset(Xd, metric=pc.IP)
+    p = pc.params(k=VMF["k"], R=VMF["R"], L_search=VMF["L"], L_dep=VMF["L"], center=pc.CENTER_PRODUCT,
+                  n_clusters=VMF["n_clusters"], index=pc.INDEX_BRUTE_FORCE)
+    path = Path(ds, None, p, dev)
+    path.step(None)
     torch.cuda.synchronize()
-    tb0 = time.perf_counter()
-    G, _ = pc.pecann_build_graph(ds, p, order=torch.from_numpy(order).to(dev), ws=ws)
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - tb0
-
-    dens_out = dict(knn_ids=torch.empty((n, p.k), dtype=torch.int32, device=dev),
-                    knn_dist=torch.empty((n, p.k), dtype=torch.float32, device=dev),
-                    density=torch.empty(n, dtype=torch.float32, device=dev),
-                    rank_key=torch.empty(n, dtype=torch.float32, device=dev))
-    dep_out = dict(dep=torch.empty(n, dtype=torch.int32, device=dev),
-                   dep_dist=torch.empty(n, dtype=torch.float32, device=dev))
-    labels = torch.empty(n, dtype=torch.int32, device=dev)
-    cws = torch.empty(8 * n + (1 << 20), dtype=torch.uint8, device=dev)
-    def step():
-        pc.pecann_density(ds, G, p, ws=ws, out=dens_out)
-        pc.pecann_dependent_points(ds, G, p, dens_out["rank_key"], dens_out["knn_ids"], dens_out["knn_dist"],
-                                   ws=ws, out=dep_out)
-        pc.pecann_cluster(dens_out["density"], dep_out["dep"], dep_out["dep_dist"], p, ws=cws, count=False,
-                          labels=labels)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    timed_density = []
     barrier()
     torch.cuda.synchronize()
     l0 = pc.pecann_kernel_launches()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(args.steps):
-        torch.cuda.nvtx.range_push("pecann_step")
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pc.pecann_density(ds, G, p, ws=ws, out=dens_out)
-        e1.record(stream)
-        pc.pecann_dependent_points(ds, G, p, dens_out["rank_key"], dens_out["knn_ids"], dens_out["knn_dist"],
-                                   ws=ws, out=dep_out)
-        pc.pecann_cluster(dens_out["density"], dep_out["dep"], dep_out["dep_dist"], p, ws=cws, count=False,
-                          labels=labels)
-        timed_density.append((e0, e1))
-        torch.cuda.nvtx.range_pop()
-    t1.record(stream)
-    torch.cuda.synchronize()
+    elapsed, dens_ms = timed(path.step, args.warmup, args.steps, stream)
     barrier()
     launches = pc.pecann_kernel_launches() - l0
     clk = clocks.stop()
-    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1000.0, dist, dev)
-    dens_avg_s = float(np.mean([a.elapsed_time(b) for a, b in timed_density])) / 1000.0
-    value = replica_throughput(n, args.steps, world, elapsed)
-    stats = pc.pecann_dependent_points(ds, G, p, dens_out["rank_key"], dens_out["knn_ids"], dens_out["knn_dist"],
-                                       ws=ws, out=dep_out)["stats"]
+    elapsed = max_over_ranks(elapsed, dist, dev)
+    counts = path.screen_counts()  # of the last dependent call
+    path.pc.pecann_density(ds, None, p, ws=path.ws, out=path.dens)
+    knn_counts = path.screen_counts()
     torch.cuda.synchronize()
-
-    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-              "warmup": args.warmup, "ms_per_step": elapsed * 1000 / args.steps, "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-              "config": {"workload": WORKLOAD_NAME if n == WORKLOAD["n"] else WORKLOAD_NAME.replace(
-                  "1,000,000", f"{n:,}"), "n": n, "d": WORKLOAD["d"], "R": p.R, "L": p.L_search, "k": p.k,
-                  "alpha": WORKLOAD["alpha"], "dep_threshold": p.dep_threshold, "L_build": p.L_build,
-                  "n_start": p.n_start, "build_passes": p.build_passes,
-                  "parallelism": "replicas" if world > 1 else "single-gpu",
-                  "l2": "inputs (128 MB rows + 256 MB graph) exceed the 129 MB L2; no flush between steps"},
-              "gpu_launches": int(launches), "clocks": clk, "build_s": build_s,
-              "dep_rounds": int(stats[0]), "unfinished_after_round0": int(stats[1]),
-              "brute_force_tail": int(stats[63]), "density_ms": dens_avg_s * 1000}
-
+    name = VMF_NAME if n == VMF["n"] else VMF_NAME.replace("1,280,000", f"{n:,}")
+    result = {"metric": METRIC, "value": replica_throughput(n, args.steps, world, elapsed), "unit": UNIT,
+              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": elapsed * 1000 / args.steps, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": name, "index": "brute force (exact; BF16 tcgen05 screen, FP32 canonical decision)",
+                         "n": n, "d": VMF["d"], "k": VMF["k"], "metric": "inner product",
+                         "parallelism": "replicas" if world > 1 else "single-gpu",
+                         "l2": "inputs (5.2 GB FP32 rows) exceed the 129 MB L2; no flush between steps"},
+              "gpu_launches": int(launches), "clocks": clk, "density_ms": dens_ms,
+              "unfinished_after_round0": int(path.stats[1]), "screen_collect_rows_knn": knn_counts[0],
+              "screen_simt_rows_knn": knn_counts[1], "screen_collect_rows_dep": counts[0],
+              "screen_simt_rows_dep": counts[1],
+              "roofline": screen_roofline(n, VMF["d"], knn_counts[0], dens_ms / 1e3, traffic_tag="k_bf_screen_vmf1024")}
     if rank == 0 and not args.quick:
         import oracle
         from oracle import exact
 
         oracle.build()
-        # ---- sampled exact k-NN recall (FP64 brute force on 2000 queries)
-        qs = synth.sample_ids(n, 2000)
-        _, ex_d = exact.exact_knn_queries(X, qs, p.k)
-        got = dens_out["knn_dist"][torch.from_numpy(qs).to(dev)].cpu().numpy()
-        result["recall"] = exact.knn_recall(got, ex_d)
-        result["ari_vs_generator"] = exact.ari(labels.cpu().numpy(), gt)
-        # ---- roofline of the dominant kernel (the k-NN beam search of the density pass)
-        Gh = G.cpu().numpy()
-        P = oracle.Points(X)
-        e_q, c_q = oracle.search_counts(P, Gh, synth.sample_ids(n, 2000, seed=99), L=p.L_search)
-        row = WORKLOAD["d"] * 1
-        bytes_q = e_q.mean() * 4 * p.R + (c_q.mean() + 1) * row + 8 * p.k + 8
-        alg_bytes = bytes_q * n
-        pk, src = peaks()
-        achieved = alg_bytes / dens_avg_s / 1e9
-        result["roofline"] = {"kernel": "k_search (k-NN + density pass)", "bound": "hbm", "achieved": achieved,
-                              "peak": pk["hbm_gbs"], "peak_source": src, "unit": "GB/s",
-                              "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic("k_search_density_c2"),
-                              "algorithmic_bytes_per_launch": alg_bytes, "E_q": float(e_q.mean()),
-                              "C_q": float(c_q.mean())}
-        # ---- end to end through the public API from pinned host buffers
-        Xh = torch.from_numpy(X).pin_memory()
-        Gh_t = G.cpu().pin_memory()
-        rho_h = torch.empty(n, dtype=torch.float32).pin_memory()
-        dep_h = torch.empty(n, dtype=torch.int32).pin_memory()
-        dd_h = torch.empty(n, dtype=torch.float32).pin_memory()
-        lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
-        Xd2 = torch.empty_like(Xd)
-        Gd2 = torch.empty_like(G)
-        ds2 = pc.Dataset(Xd2)
-        k_e2e = max(3, min(args.steps, 5))
-        torch.cuda.synchronize()
-        s0 = time.perf_counter()
-        for _ in range(k_e2e):
-            Xd2.copy_(Xh, non_blocking=True)
-            Gd2.copy_(Gh_t, non_blocking=True)
-            pc.pecann_density(ds2, Gd2, p, ws=ws, out=dens_out)
-            pc.pecann_dependent_points(ds2, Gd2, p, dens_out["rank_key"], dens_out["knn_ids"],
-                                       dens_out["knn_dist"], ws=ws, out=dep_out)
-            pc.pecann_cluster(dens_out["density"], dep_out["dep"], dep_out["dep_dist"], p, ws=cws, count=False,
-                              labels=labels)
-            rho_h.copy_(dens_out["density"], non_blocking=True)
-            dep_h.copy_(dep_out["dep"], non_blocking=True)
-            dd_h.copy_(dep_out["dep_dist"], non_blocking=True)
-            lab_h.copy_(labels, non_blocking=True)
-            torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - s0) / k_e2e
-        result["e2e"] = {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes + Gh.nbytes),
-                         "d2h_bytes_per_step": int(16 * n)}
-        # ---- CPU baseline: the oracle as it stands on a bounded sample
         threads = oracle.default_threads()
-        rate, _ = oracle_subset_run(args.subset, threads)
+        knn_dist = path.dens["knn_dist"].cpu().numpy()
+        exact_labels = path.labels.cpu().numpy()
+        result["recall"] = exact_recall(X, 1, knn_dist, VMF["k"])
+        result["recall_queries"] = RECALL_QUERIES
+        result["ari_vs_generator"] = exact.ari(exact_labels, gt)
+        result["e2e"] = e2e_rate(path, X, None, max(2, min(args.steps, 3)))
+        rate, dt = cpu_knn_rate(X, 1, None, 0, VMF["k"], CPU_SAMPLE, threads)
         result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                  "sample": (f"oracle k-NN+density, dependent points and clusters on a "
-                                             f"{args.subset}-point sample of the same generator, on its own "
-                                             f"graph (built untimed); one step")}
+                                  "sample": (f"oracle brute-force index (exact k-NN + kth density) of {CPU_SAMPLE} "
+                                             f"sampled points over all {n:,} rows of the same workload; the "
+                                             f"dependent step is not in the sample (an upper bound)")}
+        # ---- variants: the same rows on a Vamana graph, FP32 / BF16 / FP8 traversal
+        result["variants"] = vmf_graph_variants(args, X, Xd, knn_dist, exact_labels, dev, stream, threads)
+        del path
+        torch.cuda.empty_cache()
+        # ---- the uint8 workload on its graph and on the exact index
+        del Xd, ds
+        torch.cuda.empty_cache()
+        result["variants"] += u8_variants(args, dev, stream, threads)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def vmf_graph_variants(args, X, Xd, exact_dist, exact_labels, dev, stream, threads):
+    import torch
+
+    from oracle import exact
+    from paper_2312_03940_gb300 import pecann as pc
+    from paper_2312_03940_gb300 import synth
+
+    n = len(X)
+    p = pc.params(k=VMF["k"], R=VMF["R"], L_build=VMF["L_build"], L_search=VMF["L"], L_dep=VMF["L"],
+                  alpha=VMF["alpha"], build_passes=VMF["build_passes"], n_start=min(n, VMF["n_start"] * n // VMF["n"]),
+                  center=pc.CENTER_PRODUCT, n_clusters=VMF["n_clusters"])
+    ds32 = pc.Dataset(Xd, metric=pc.IP)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G, _ = pc.pecann_build_graph(ds32, p, order=torch.from_numpy(synth.insertion_order(n)).to(dev))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Gh = G.cpu().numpy()
+    Xb = Xd.to(torch.bfloat16).contiguous()
+    scale = (Xd.abs().amax(0) / 448.0).clamp_min(torch.finfo(torch.float32).tiny).contiguous()
+    Xf8 = (Xd / scale).to(torch.float8_e4m3fn).contiguous()
+    kinds = [("fp32", ds32, 4), ("bf16", pc.Dataset(Xb, metric=pc.IP, data_f32=Xd), 2),
+             ("fp8-e4m3", pc.Dataset(Xf8, metric=pc.IP, dim_scale=scale, data_f32=Xd), 1)]
+    out = []
+    base_name = VMF_NAME if n == VMF["n"] else VMF_NAME.replace("1,280,000", f"{n:,}")
+    rate_cpu, _ = cpu_knn_rate(X, 1, Gh, VMF["L"], VMF["k"], CPU_SAMPLE_GRAPH, threads)
+    for tag, ds, s in kinds:
+        path = Path(ds, G, p, dev)
+        el, dms = timed(path.step, 1, args.variant_steps, stream)
+        got = path.dens["knn_dist"].cpu().numpy()
+        line = {"metric": METRIC, "value": n / (el / args.variant_steps), "unit": UNIT, "dtype": tag,
+                "ms_per_step": el * 1000 / args.variant_steps, "steps": args.variant_steps, "warmup": 1,
+                "config": {"workload": base_name, "index": f"Vamana graph R={VMF['R']} beam {VMF['L']} "
+                                                          f"(build: {VMF['build_passes']} passes, beam {VMF['L_build']}, "
+                                                          f"{p.n_start} start points)",
+                           "traversal": tag + ("" if tag == "fp32" else " rows, exact FP32 re-rank")},
+                "density_ms": dms, "build_s": build_s,
+                "recall_full_n_vs_exact_index": full_recall(got, exact_dist),
+                "ari_vs_exact_index": exact.ari(path.labels.cpu().numpy(), exact_labels),
+                "below_recall_bar": True,
+                "roofline": graph_roofline(X, 1, Gh, p, VMF["d"] * s, dms / 1e3, n,
+                                           f"k_search ({tag} rows, k-NN + density pass)",
+                                           traffic_tag=f"k_search_vmf1024_{tag}"),
+                "cpu_baseline": {"value": rate_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": (f"oracle beam search (Algorithm 1, FP32) k-NN + kth density of "
+                                            f"{CPU_SAMPLE_GRAPH} sampled points on the same graph")}}
+        out.append(line)
+        del path
+        torch.cuda.empty_cache()
+    return out
+
+
+def u8_variants(args, dev, stream, threads):
+    import torch
+
+    from oracle import exact
+    from paper_2312_03940_gb300 import pecann as pc
+    from paper_2312_03940_gb300 import synth
+
+    n = U8["n"] if not args.n else min(args.n, U8["n"])
+    X, gt = u8_data(n)
+    Xd = torch.from_numpy(X).to(dev)
+    ds = pc.Dataset(Xd)
+    p = pc.params(k=U8["k"], R=U8["R"], L_build=U8["L_build"], L_search=U8["L"], L_dep=U8["L"], alpha=U8["alpha"],
+                  n_start=min(n, U8["n_start"]), build_passes=U8["build_passes"], center=pc.CENTER_PRODUCT,
+                  n_clusters=U8["n_clusters"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G, _ = pc.pecann_build_graph(ds, p, order=torch.from_numpy(synth.insertion_order(n)).to(dev))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Gh = G.cpu().numpy()
+    name = U8_NAME if n == U8["n"] else U8_NAME.replace("1,000,000", f"{n:,}")
+    out = []
+    # graph path (beam 128)
+    path = Path(ds, G, p, dev)
+    steps = max(args.variant_steps, 5)
+    el, dms = timed(path.step, 2, steps, stream)
+    graph_dist = path.dens["knn_dist"].cpu().numpy()
+    graph_labels = path.labels.cpu().numpy()
+    rate_cpu, _ = cpu_knn_rate(X, 0, Gh, U8["L"], U8["k"], CPU_SAMPLE_GRAPH * 4, threads)
+    line = {"metric": METRIC, "value": n / (el / steps), "unit": UNIT, "dtype": "u8",
+            "ms_per_step": el * 1000 / steps, "steps": steps, "warmup": 2,
+            "config": {"workload": name, "index": f"Vamana graph R={U8['R']} beam {U8['L']} (build: 2 passes, "
+                                                  f"beam {U8['L_build']}, {p.n_start} start points)"},
+            "density_ms": dms, "build_s": build_s, "dep_rounds": int(path.stats[0]),
+            "unfinished_after_round0": int(path.stats[1]), "brute_force_tail": int(path.stats[63]),
+            "recall": exact_recall(X, 0, graph_dist, U8["k"], m=2000), "recall_queries": 2000,
+            "roofline": graph_roofline(X, 0, Gh, p, U8["d"], dms / 1e3, n, "k_search (k-NN + density pass)",
+                                       traffic_tag="k_search_density_c2"),
+            "e2e": e2e_rate(path, X, G.cpu(), 3),
+            "cpu_baseline": {"value": rate_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": (f"oracle beam search (Algorithm 1) k-NN + kth density of "
+                                        f"{CPU_SAMPLE_GRAPH * 4} sampled points on the same graph")}}
+    del path
+    # exact index on the same rows
+    pb = pc.params(k=U8["k"], R=U8["R"], L_search=U8["L"], L_dep=U8["L"], center=pc.CENTER_PRODUCT,
+                   n_clusters=U8["n_clusters"], index=pc.INDEX_BRUTE_FORCE)
+    path = Path(ds, None, pb, dev)
+    el, dms = timed(path.step, 1, args.variant_steps, stream)
+    knn_counts = path.screen_counts()
+    ex_dist = path.dens["knn_dist"].cpu().numpy()
+    line["recall_full_n_vs_exact_index"] = full_recall(graph_dist, ex_dist)
+    line["ari_vs_exact_index"] = exact.ari(graph_labels, path.labels.cpu().numpy())
+    out.append(line)
+    rate_cpu_bf, _ = cpu_knn_rate(X, 0, None, 0, U8["k"], CPU_SAMPLE * 4, threads)
+    out.append({"metric": METRIC, "value": n / (el / args.variant_steps), "unit": UNIT, "dtype": "u8",
+                "ms_per_step": el * 1000 / args.variant_steps, "steps": args.variant_steps, "warmup": 1,
+                "config": {"workload": name, "index": "brute force (exact; BF16 tcgen05 screen, exact integer decision)"},
+                "density_ms": dms, "recall": 1.0, "ari_vs_generator": exact.ari(path.labels.cpu().numpy(), gt),
+                "roofline": screen_roofline(n, U8["d"], knn_counts[0], dms / 1e3, traffic_tag="k_bf_screen_u8"),
+                "cpu_baseline": {"value": rate_cpu_bf, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": f"oracle brute-force index k-NN + kth density of {CPU_SAMPLE * 4} sampled "
+                                           f"points over all {n:,} rows"}})
+    return out
+
+
+def run_u8_only(args):
+    """The uint8 workload alone on its graph and on the exact index (report)."""
+    import torch
+
+    from paper_2312_03940_gb300 import build as pbuild
+    from paper_2312_03940_gb300 import pecann as pc
+
+    pbuild.build()
+    pc.load_library()
+    import oracle
+
+    oracle.build()
+    out = u8_variants(args, torch.device("cuda", 0), torch.cuda.current_stream(), oracle.default_threads())
+    print(json.dumps({"workload": "u8-1m", "lines": out}), flush=True)
 
 
 # ---------------------------------------------------------------- extra report workloads
@@ -491,8 +716,8 @@ def run_batched64(args):
 
 
 def run_reduced(args, kind):
-    """FP32 traversal vs BF16 (and, for inner product, FP8 e4m3 with per-dimension
-    scales) traversal with exact FP32 re-rank, on the same graph."""
+    """The 1M x 384 power-law sphere (L2): FP32 vs BF16 traversal with exact
+    FP32 re-rank on the same graph, kth and exp-sum densities."""
     import torch
 
     from oracle import exact
@@ -500,18 +725,11 @@ def run_reduced(args, kind):
     from paper_2312_03940_gb300 import synth
 
     pc.load_library()
-    if kind == "sphere384":
-        n = args.n if args.n != WORKLOAD["n"] else 1_000_000
-        X, gt = synth.powerlaw_sphere(n=n)
-        metric, R, L, k, alpha, ncl = pc.L2, 48, 128, 20, 1.1, 10_000
-        dens_fns = [("kth", pc.DENS_KTH), ("exp-sum", pc.DENS_EXPSUM)]
-        desc = f"unit-norm power-law-spectrum sphere n={n} d=384, 10,000 Pareto(1.5) clusters; R=48 L=128 alpha=1.1 k=20"
-    else:
-        n = args.n if args.n != WORKLOAD["n"] else 1_280_000
-        X, gt = synth.vmf_like(n=n)
-        metric, R, L, k, alpha, ncl = pc.IP, 64, 200, 16, 1.2, 1000
-        dens_fns = [("kth", pc.DENS_KTH)]
-        desc = f"unit-norm vMF-like n={n} d=1024 inner product, 1,000 clusters; R=64 L=200 k=16"
+    n = args.n or 1_000_000
+    X, gt = synth.powerlaw_sphere(n=n)
+    metric, R, L, k, alpha, ncl = pc.L2, 48, 128, 20, 1.1, 10_000
+    dens_fns = [("kth", pc.DENS_KTH), ("exp-sum", pc.DENS_EXPSUM)]
+    desc = f"unit-norm power-law-spectrum sphere n={n} d=384, 10,000 Pareto(1.5) clusters; R=48 L=128 alpha=1.1 k=20"
     Xd = torch.from_numpy(X).cuda()
     del X
     Xb = Xd.to(torch.bfloat16).contiguous()
@@ -571,8 +789,10 @@ def main():
         run_reference(args)
     elif args.workload == "batched64":
         run_batched64(args)
-    elif args.workload in ("sphere384", "vmf1024"):
-        run_reduced(args, args.workload)
+    elif args.workload == "sphere384":
+        run_reduced(args, "sphere384")
+    elif args.workload == "u8-1m":
+        run_u8_only(args)
     else:
         run_ours(args)
 
