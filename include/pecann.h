@@ -144,7 +144,9 @@ typedef struct {
   int32_t rerank_k;          /* BF16 traversal: candidates per point re-scored in FP32
                                 (0: min(L_search, 4k); must be >= k)         density          */
   int32_t block_warps;       /* warps per block of the search kernel (1, 2, 4 or 8; 0 =
-                                automatic). Like hash_slots it changes speed, never results */
+                                automatic); with the brute-force index, CTAs per cluster of
+                                its k-NN screen (1, 2 or 4; 0 = automatic). Like hash_slots
+                                it changes speed, never results                            */
   int32_t index;             /* PECANN_INDEX_GRAPH (the Vamana graph given to the call) or
                                 PECANN_INDEX_BRUTE_FORCE (no index, exact; the graph may be
                                 NULL)                                      density, dependent */
@@ -298,9 +300,12 @@ typedef struct {
  * above each of their k nearest neighbours (the n x k d_knn_ids of
  * pecann_density, -1 entries ignored; rank by d_rank_key, ties to the smaller
  * id); d_knn_ids and d_rank_key may be NULL when no setting uses it.
- * n_settings in 1..4096. If h_n_clusters (HOST, n_settings entries) is not
- * NULL it receives each setting's number of clusters and the call waits for
- * the stream. Workspace: pecann_cluster_workspace_size(n, n_settings).
+ * n_settings in 1..4096. All settings run in the same passes: one launch
+ * per radix pass of the product-center selection for every product setting,
+ * one launch for every setting's parent array, and pointer-jumping sweeps
+ * over all n_settings x n entries. If h_n_clusters (HOST, n_settings entries)
+ * is not NULL it receives each setting's number of clusters and the call
+ * waits for the stream. Workspace: pecann_cluster_workspace_size(n, n_settings).
  * Errors: PECANN_EINVAL for a bad setting (unknown center function,
  * n_clusters < 1 with the product center, a local center without k-NN lists)
  * -- checked on the host before any GPU work.

@@ -19,6 +19,11 @@ cudaError_t run_cluster(int64_t n, const float* rho, const int32_t* lam, const f
                         const float* rank_key, int32_t* labels, void* ws, unsigned long long* d_roots,
                         cudaStream_t st);
 size_t cluster_ws_bytes(int64_t n);
+size_t sweep_ws_bytes(int64_t n, int S);
+cudaError_t run_cluster_sweep(int64_t n, const float* rho, const int32_t* lam, const float* delta, int S,
+                              const pecann_cluster_setting* h_set, const int32_t* knn_ids, int k,
+                              const float* rank_key, int32_t* labels, void* ws, unsigned long long* d_roots,
+                              cudaStream_t st);
 size_t build_ws_bytes(int64_t n, const pecann_params& p, int64_t cap, int vcap);
 int64_t batch_cap_of(int64_t n, float frac);
 cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t* d_order, int32_t* G,
@@ -192,7 +197,7 @@ static size_t bf_density_offset(int64_t n) { return 2 * al((size_t)n * 4); }
 static size_t bf_dep_offset(int64_t n) { return 2 * al((size_t)n * 4) + al((size_t)n * 8); }
 
 // The brute-force index reads BF16 copies of the rows through TMA (rows of
-// d * 2 bytes, a multiple of 16) and keeps 64 candidates per query.
+// d * 2 bytes, a multiple of 16) and keeps 80 candidates per query.
 pecann_status check_index(const DataView& dv, const pecann_params* p) {
   if (p->index != PECANN_INDEX_GRAPH && p->index != PECANN_INDEX_BRUTE_FORCE)
     return set_last_error("index must be PECANN_INDEX_GRAPH or PECANN_INDEX_BRUTE_FORCE"), PECANN_EINVAL;
@@ -651,13 +656,15 @@ pecann_status pecann_cluster(int64_t n, const float* d_density, const int32_t* d
   return PECANN_OK;
 }
 
-static size_t sweep_counts_offset(int64_t n) { return (HDR + cluster_ws_bytes(n) + 255) & ~(size_t)255; }
+static size_t sweep_counts_offset(int64_t n, int32_t n_settings) {
+  return (HDR + sweep_ws_bytes(n, n_settings) + 255) & ~(size_t)255;
+}
 
 pecann_status pecann_cluster_workspace_size(int64_t n, int32_t n_settings, size_t* bytes) {
   if (!bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
   if (n < 1 || n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
   if (n_settings < 1 || n_settings > 4096) return set_last_error("n_settings must be in 1..4096"), PECANN_EINVAL;
-  *bytes = sweep_counts_offset(n) + (size_t)n_settings * 8;
+  *bytes = sweep_counts_offset(n, n_settings) + (size_t)n_settings * 8;
   return PECANN_OK;
 }
 
@@ -682,17 +689,15 @@ pecann_status pecann_cluster_sweep(int64_t n, const float* d_density, const int3
   }
   if (ws_bytes < need) return set_last_error("workspace too small"), PECANN_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned long long* counts = (unsigned long long*)((uint8_t*)ws + sweep_counts_offset(n));
-  for (int32_t i = 0; i < n_settings; i++) {
-    const pecann_cluster_setting& c = h_settings[i];
-    cudaError_t e = run_cluster(n, d_density, d_dep, d_dep_dist, c.center, c.rho_min, c.delta_min, c.n_clusters,
-                                d_knn_ids, k, d_rank_key, d_labels + (int64_t)i * n, (uint8_t*)ws + HDR,
-                                h_n_clusters ? counts + i : nullptr, st);
-    if ((s = cuda_status(e, "cluster sweep"))) return s;
-  }
+  unsigned long long* counts = (unsigned long long*)((uint8_t*)ws + sweep_counts_offset(n, n_settings));
+  // every setting in the same passes: shared select passes, one parent
+  // launch and shared pointer-jumping sweeps
+  cudaError_t e = run_cluster_sweep(n, d_density, d_dep, d_dep_dist, n_settings, h_settings, d_knn_ids, k,
+                                    d_rank_key, d_labels, (uint8_t*)ws + HDR, h_n_clusters ? counts : nullptr, st);
+  if ((s = cuda_status(e, "cluster sweep"))) return s;
   if (h_n_clusters) {
     std::vector<unsigned long long> r((size_t)n_settings);
-    cudaError_t e = cudaMemcpyAsync(r.data(), counts, (size_t)n_settings * 8, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(r.data(), counts, (size_t)n_settings * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if ((s = cuda_status(e, "readback"))) return s;
     for (int32_t i = 0; i < n_settings; i++) h_n_clusters[i] = (int64_t)r[i];

@@ -31,7 +31,7 @@
 //                TMEM accumulators;
 //   warps 2..9   epilogue: two threads per query row (row = TMEM lane; the
 //                warp's lane quarter), each reading one 128-column half of a
-//                finished tile. A thread keeps the 32 smallest keys of its
+//                finished tile. A thread keeps the SC_HALF smallest keys of its
 //                half in a max-heap in shared memory (slot-major, so that
 //                neighbouring threads hit neighbouring banks); a 32-column
 //                chunk is first reduced to its smallest key and only chunks
@@ -54,8 +54,8 @@ constexpr int SC_M = 128;          // query rows per tile (TMEM lanes)
 constexpr int SC_N = 256;          // point rows per tile (TMEM columns per accumulator)
 constexpr int SC_KCH = 64;         // BF16 columns per chunk (one 128-byte swizzle row)
 constexpr int SC_STAGES = 3;
-constexpr int SC_KEEP = 64;        // kept candidates per query (two halves of SC_HALF)
-constexpr int SC_HALF = 32;        // heap entries per epilogue thread
+constexpr int SC_HALF = 40;        // heap entries per epilogue thread
+constexpr int SC_KEEP = 2 * SC_HALF;  // kept candidates per query (two halves)
 constexpr int SC_EPI = 256;        // epilogue threads (8 warps)
 constexpr int SC_THREADS = 64 + SC_EPI;
 constexpr uint32_t SC_A_BYTES = SC_M * SC_KCH * 2;   // 16 KB
@@ -182,14 +182,21 @@ __device__ __forceinline__ void heap_sort(float* hk, int32_t* hi, int et, int cn
   }
 }
 
-template <int MODE, int PASS, int METRIC>
+// CL: CTAs per cluster. With CL > 1 the CTAs of a cluster take CL
+// consecutive query tiles and sweep the point tiles in lockstep: each loads
+// 1/CL of every point chunk (tb's box is SC_N / CL rows) and multicasts it to
+// all of them, so a point chunk leaves L2 once per cluster; a stage is free
+// again once every CTA's MMAs have read it (each MMA commit arrives on the
+// stage's empty barrier in every CTA of the cluster). A CTA whose query tile
+// lies past the last one still takes part, on rows that read as zeros and
+// produce no output.
+template <int MODE, int PASS, int METRIC, int CL>
 __global__ void __launch_bounds__(SC_THREADS, 1)
     k_bf_screen(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, ScreenArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* hk = reinterpret_cast<float*>(ring + SC_STAGES * SC_STAGE_BYTES);  // [SC_HALF][SC_EPI]
   int32_t* hi = reinterpret_cast<int32_t*>(hk + SC_HALF * SC_EPI);          // [SC_HALF][SC_EPI]
-  float* meta = reinterpret_cast<float*>(hi + SC_HALF * SC_EPI);           // [2][norms SC_N | keys SC_N]
   __shared__ __align__(8) uint64_t full_bar[SC_STAGES], empty_bar[SC_STAGES];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], final_bar;
   __shared__ uint32_t tmem_slot;
@@ -200,12 +207,17 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_qt = (a.nq + SC_M - 1) / SC_M;
   const int64_t n_pt = (a.n + SC_N - 1) / SC_N;
+  // query tiles: group g (of CL tiles) goes to cluster g mod (clusters);
+  // the CTA of rank `crank` takes tile g * CL + crank
+  const int64_t crank = CL > 1 ? (int64_t)tc::cluster_rank() : 0;
+  const int64_t n_cl = gridDim.x / CL, cl_id = blockIdx.x / CL;
+  constexpr uint16_t cl_mask = (uint16_t)((1u << CL) - 1);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < SC_STAGES; s++) {
       tc::mbar_init(&full_bar[s], 1);
-      tc::mbar_init(&empty_bar[s], 1);
+      tc::mbar_init(&empty_bar[s], CL);
     }
     for (int b = 0; b < 2; b++) {
       tc::mbar_init(&tfull_bar[b], 1);
@@ -221,6 +233,7 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (CL > 1) tc::cluster_sync();  // every peer's barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
 
@@ -231,7 +244,8 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
       tc::prefetch_tmap(&tb);
       uint64_t it = 0;  // chunk loads issued
       bool ok = true;
-      for (int64_t qt = blockIdx.x; qt < n_qt && ok; qt += gridDim.x) {
+      for (int64_t g = cl_id; g * CL < n_qt && ok; g += n_cl) {
+        const int64_t qt = g * CL + crank;
         for (int64_t pt = 0; pt < n_pt && ok; pt++) {
           for (int c = 0; c < a.kc; c++) {
             const int s = (int)(it % SC_STAGES);
@@ -243,7 +257,11 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
             uint8_t* st = ring + (size_t)s * SC_STAGE_BYTES;
             tc::mbar_arrive_expect_tx(&full_bar[s], SC_STAGE_BYTES);
             tc::tma_load_2d(st, &ta, c * SC_KCH, (int32_t)(qt * SC_M), &full_bar[s]);
-            tc::tma_load_2d(st + SC_A_BYTES, &tb, c * SC_KCH, (int32_t)(pt * SC_N), &full_bar[s]);
+            if (CL == 1)
+              tc::tma_load_2d(st + SC_A_BYTES, &tb, c * SC_KCH, (int32_t)(pt * SC_N), &full_bar[s]);
+            else
+              tc::tma_load_2d_mc(st + SC_A_BYTES + crank * (SC_B_BYTES / CL), &tb, c * SC_KCH,
+                                 (int32_t)(pt * SC_N + crank * (SC_N / CL)), &full_bar[s], cl_mask);
             it++;
           }
         }
@@ -261,7 +279,7 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
       const uint32_t idesc = tc::idesc_bf16_f32(SC_M, SC_N);
       uint64_t it = 0, tile = 0;
       bool ok = true;
-      for (int64_t qt = blockIdx.x; qt < n_qt && ok; qt += gridDim.x) {
+      for (int64_t g = cl_id; g * CL < n_qt && ok; g += n_cl) {
         for (int64_t pt = 0; pt < n_pt && ok; pt++, tile++) {
           const int b = (int)(tile & 1);
           if (!tc::mbar_wait(&tempty_bar[b], (uint32_t)(((tile >> 1) & 1) ^ 1), &abort_flag, SC_WAIT_NS)) {
@@ -281,7 +299,10 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < SC_KCH / 16; k++)
               tc::mma_bf16(dacc, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k), idesc, (c | k) != 0);
-            tc::mma_commit(&empty_bar[s]);
+            if (CL == 1)
+              tc::mma_commit(&empty_bar[s]);
+            else
+              tc::mma_commit_mc(&empty_bar[s], cl_mask);
           }
           if (ok) tc::mma_commit(&tfull_bar[b]);
         }
@@ -301,7 +322,8 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
     const float M = __ldg(a.maxnorm);
     uint64_t tile = 0;
     bool ok = true;
-    for (int64_t qt = blockIdx.x; qt < n_qt && ok; qt += gridDim.x) {
+    for (int64_t g = cl_id; g * CL < n_qt && ok; g += n_cl) {
+      const int64_t qt = g * CL + crank;
       const int64_t r = qt * SC_M + rl;
       const bool valid = r < a.nq;
       const int32_t qid = valid ? (a.qids ? __ldg(a.qids + r) : (int32_t)r) : -1;
@@ -314,18 +336,7 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
       for (int64_t pt = 0; pt < n_pt; pt++, tile++) {
         const int b = (int)(tile & 1);
         const int64_t j0 = pt * SC_N;
-        // per-column data of this tile (squared norms, rank keys), double
-        // buffered by tile parity; the one barrier per tile also makes the
-        // decision to give up uniform over the epilogue threads
-        float* mt = meta + b * 2 * SC_N;
-        if (METRIC == MET_L2 || MODE == SCR_DEP) {
-          const int c = et;
-          const int64_t j = j0 + c;
-          if (METRIC == MET_L2) mt[c] = j < a.n ? __ldg(a.pnorm2 + j) : 0.0f;
-          if (MODE == SCR_DEP) mt[SC_N + c] = j < a.n ? __ldg(a.rank_key + j) : 0.0f;
-        }
-        const bool got = tc::mbar_wait(&tfull_bar[b], (uint32_t)((tile >> 1) & 1), &abort_flag, SC_WAIT_NS);
-        if (epi_sync_or(!got)) {
+        if (!tc::mbar_wait(&tfull_bar[b], (uint32_t)((tile >> 1) & 1), &abort_flag, SC_WAIT_NS)) {
           ok = false;
           break;
         }
@@ -334,29 +345,75 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
         for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 32) {
           float v[32];
           tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * SC_N + c0), v);
-          // approximate keys, smaller = closer: -<x, y> (IP), |y|^2 - 2 <x, y> (L2)
-          float mn = INFINITY;
+          // approximate keys, smaller = closer: -<x, y> (IP), |y|^2 - 2 <x, y>
+          // (L2: the squared norms, padded past n, read four at a time
+          // through L1, the same addresses for the whole warp); the chunk's
+          // best key by a tree of depth 5
+          if (MODE == SCR_DEP) {
+            // only points ranked above the query count: the others get the
+            // worst key (rank keys padded past n with NaN, never above)
+            const float4* k4 = reinterpret_cast<const float4*>(a.rank_key + j0 + c0);
+            // (as a product: -inf, which gives key +inf under both metrics)
+            const float worst = -INFINITY;
 #pragma unroll
-          for (int t = 0; t < 32; t++) {
-            v[t] = METRIC == MET_L2 ? __fmaf_rn(-2.0f, v[t], mt[c0 + t]) : -v[t];
-            mn = fminf(mn, v[t]);
+            for (int q = 0; q < 8; q++) {
+              const float4 kk = __ldg(k4 + q);
+              const float kv[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+              for (int u = 0; u < 4; u++) {
+                const int32_t j = (int32_t)(j0 + c0 + 4 * q + u);
+                if (!rank_above_key(kv[u], j, qkey, qid)) v[4 * q + u] = worst;
+              }
+            }
           }
-          const bool any = PASS == SCR_COLLECT ? (mn <= thr) : (mn < thr);
-          if (!any) continue;  // the common case once the heap is full
-          const int64_t jbase = j0 + c0;
+          float w[16];
+          if (METRIC == MET_L2) {
+            const float4* m4 = reinterpret_cast<const float4*>(a.pnorm2 + j0 + c0);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+              const float4 nn = __ldg(m4 + q);
+              // a masked column carries -inf as its product: its key is +inf
+              v[4 * q + 0] = __fmaf_rn(-2.0f, v[4 * q + 0], nn.x);
+              v[4 * q + 1] = __fmaf_rn(-2.0f, v[4 * q + 1], nn.y);
+              v[4 * q + 2] = __fmaf_rn(-2.0f, v[4 * q + 2], nn.z);
+              v[4 * q + 3] = __fmaf_rn(-2.0f, v[4 * q + 3], nn.w);
+            }
+#pragma unroll
+            for (int t = 0; t < 16; t++) w[t] = fminf(v[t], v[t + 16]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 16; t++) w[t] = fmaxf(v[t], v[t + 16]);
+          }
+#pragma unroll
+          for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+            for (int t = 0; t < h; t++) w[t] = METRIC == MET_L2 ? fminf(w[t], w[t + h]) : fmaxf(w[t], w[t + h]);
+          const float best = METRIC == MET_L2 ? w[0] : -w[0];
+          if (!(PASS == SCR_COLLECT ? (best <= thr) : (best < thr))) continue;  // the common case
+          // the columns that beat the threshold, then one at a time (a
+          // compact loop: the key of column t is picked by selects)
+          uint32_t hm = 0;
 #pragma unroll
           for (int t = 0; t < 32; t++) {
-            const float key = v[t];
-            const bool hit = PASS == SCR_COLLECT ? (key <= thr) : (key < thr);
-            if (!hit) continue;
-            const int64_t j = jbase + t;
-            if (j >= a.n || j == qid) continue;
-            if (MODE == SCR_DEP && !rank_above_key(mt[SC_N + c0 + t], (int32_t)j, qkey, qid)) continue;
+            const float key = METRIC == MET_L2 ? v[t] : -v[t];
+            hm |= (uint32_t)(PASS == SCR_COLLECT ? (key <= thr) : (key < thr)) << t;
+          }
+          const int64_t jbase = j0 + c0;
+          if (jbase + 32 > a.n) hm &= jbase >= a.n ? 0u : (0xffffffffu >> (32 - (int)(a.n - jbase)));
+          if (qid >= jbase && qid < jbase + 32) hm &= ~(1u << (qid - jbase));
+          while (hm) {
+            const int t = __ffs(hm) - 1;
+            hm &= hm - 1;
+            float key = v[0];
+#pragma unroll
+            for (int i = 1; i < 32; i++) key = t == i ? v[i] : key;
+            if (METRIC != MET_L2) key = -key;
+            const int32_t j = (int32_t)(jbase + t);
             if (PASS == SCR_COLLECT) {
               const int slot = atomicAdd(&row_cnt[rl], 1);
-              if (slot < a.cap) a.out_ids[r * a.cap + slot] = (int32_t)j;
-            } else {
-              heap_push(hk, hi, et, cnt, key, (int32_t)j);
+              if (slot < a.cap) a.out_ids[r * a.cap + slot] = j;
+            } else if (key < thr) {  // thr may have dropped since the mask
+              heap_push(hk, hi, et, cnt, key, j);
               if (cnt == SC_HALF) thr = hk[et];
             }
           }
@@ -364,6 +421,9 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
         tc::fence_before_sync();
         tc::mbar_arrive(&tempty_bar[b]);
       }
+      // the decision to give up is made uniform over the epilogue threads
+      // (a thread that left the loop early reaches this barrier too)
+      if (epi_sync_or(!ok)) ok = false;
       if (!ok) break;
       // ---- the row's result: both halves of the row are complete here
       if (PASS == SCR_COLLECT) {
@@ -413,6 +473,8 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
+  // no CTA leaves while a peer may still write into its shared memory
+  if (CL > 1) tc::cluster_sync();
   if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, 2 * SC_N);
@@ -531,41 +593,79 @@ static cudaError_t make_map(CUtensorMap* m, const void* base, int64_t n, int d, 
 }
 
 static size_t screen_smem() {
-  return 1024 + (size_t)SC_STAGES * SC_STAGE_BYTES + 2 * (size_t)SC_HALF * SC_EPI * 4 + 4 * (size_t)SC_N * 4;
+  return 1024 + (size_t)SC_STAGES * SC_STAGE_BYTES + 2 * (size_t)SC_HALF * SC_EPI * 4;
 }
 
-template <int MODE, int PASS, int METRIC>
-static cudaError_t launch_screen_t(const CUtensorMap& ta, const CUtensorMap& tb, const ScreenArgs& a,
+template <int MODE, int PASS, int METRIC, int CL>
+static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int64_t n, int d, const ScreenArgs& a,
                                    cudaStream_t st) {
-  auto kern = k_bf_screen<MODE, PASS, METRIC>;
+  auto kern = k_bf_screen<MODE, PASS, METRIC, CL>;
   const size_t smem = screen_smem();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
     set_where("brute-force screen: shared-memory attribute");
     return e;
   }
+  CUtensorMap tb;  // point rows: each CTA of a cluster loads SC_N / CL rows of a tile
+  if ((e = make_map(&tb, prows, n, d, SC_N / CL)) != cudaSuccess) return e;
   const int64_t n_qt = (a.nq + SC_M - 1) / SC_M;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_qt, num_sms()));
-  kern<<<grid, SC_THREADS, smem, st>>>(ta, tb, a);
+  const int64_t groups = (n_qt + CL - 1) / CL;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.blockDim = dim3(SC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = CL > 1 ? 1 : 0;
+  // a persistent grid: as many clusters as can be resident at once (a
+  // cluster's CTAs share one GPC, so with CL > 1 that can be fewer than
+  // SMs / CL), never more than there are groups of query tiles
+  int64_t resident = std::max<int64_t>(1, num_sms() / CL);
+  if (CL > 1) {
+    cfg.gridDim = dim3((unsigned)(CL * resident));
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc > 0) resident = nc;
+    cudaGetLastError();
+  }
+  cfg.gridDim = dim3((unsigned)(CL * std::max<int64_t>(1, std::min<int64_t>(groups, resident))));
+  e = cudaLaunchKernelEx(&cfg, kern, ta, tb, a);
   note_launch();
-  return cudaGetLastError();
+  if (e != cudaSuccess) set_where("brute-force screen: launch");
+  return e;
 }
 
-static cudaError_t launch_screen(int mode, int pass, int metric, const CUtensorMap& ta, const CUtensorMap& tb,
-                                 const ScreenArgs& a, cudaStream_t st) {
+// cl: CTAs per cluster for the k-NN keep pass (1, 2 or 4; 0 = automatic,
+// 1: measured on the 1.28M x 1024 and 1M x 128 sets, the screen is bound by
+// its MMAs and epilogue, not by L2 traffic, and clusters of 2 and 4 were no
+// faster); the other passes run few query tiles and use 1.
+static cudaError_t launch_screen(int mode, int pass, int metric, const CUtensorMap& ta, const void* prows, int64_t n,
+                                 int d, const ScreenArgs& a, int cl, cudaStream_t st) {
   if (a.nq <= 0) return cudaSuccess;
+  if (cl != 1 && cl != 2 && cl != 4) cl = 1;
+  if (mode != SCR_KNN || pass != SCR_KEEP) cl = 1;
   if (metric == MET_IP) {
-    if (mode == SCR_KNN)
-      return pass == SCR_KEEP ? launch_screen_t<SCR_KNN, SCR_KEEP, MET_IP>(ta, tb, a, st)
-                              : launch_screen_t<SCR_KNN, SCR_COLLECT, MET_IP>(ta, tb, a, st);
-    return pass == SCR_KEEP ? launch_screen_t<SCR_DEP, SCR_KEEP, MET_IP>(ta, tb, a, st)
-                            : launch_screen_t<SCR_DEP, SCR_COLLECT, MET_IP>(ta, tb, a, st);
+    if (mode == SCR_KNN && pass == SCR_KEEP) {
+      if (cl == 4) return launch_screen_t<SCR_KNN, SCR_KEEP, MET_IP, 4>(ta, prows, n, d, a, st);
+      if (cl == 2) return launch_screen_t<SCR_KNN, SCR_KEEP, MET_IP, 2>(ta, prows, n, d, a, st);
+      return launch_screen_t<SCR_KNN, SCR_KEEP, MET_IP, 1>(ta, prows, n, d, a, st);
+    }
+    if (mode == SCR_KNN) return launch_screen_t<SCR_KNN, SCR_COLLECT, MET_IP, 1>(ta, prows, n, d, a, st);
+    return pass == SCR_KEEP ? launch_screen_t<SCR_DEP, SCR_KEEP, MET_IP, 1>(ta, prows, n, d, a, st)
+                            : launch_screen_t<SCR_DEP, SCR_COLLECT, MET_IP, 1>(ta, prows, n, d, a, st);
   }
-  if (mode == SCR_KNN)
-    return pass == SCR_KEEP ? launch_screen_t<SCR_KNN, SCR_KEEP, MET_L2>(ta, tb, a, st)
-                            : launch_screen_t<SCR_KNN, SCR_COLLECT, MET_L2>(ta, tb, a, st);
-  return pass == SCR_KEEP ? launch_screen_t<SCR_DEP, SCR_KEEP, MET_L2>(ta, tb, a, st)
-                          : launch_screen_t<SCR_DEP, SCR_COLLECT, MET_L2>(ta, tb, a, st);
+  if (mode == SCR_KNN && pass == SCR_KEEP) {
+    if (cl == 4) return launch_screen_t<SCR_KNN, SCR_KEEP, MET_L2, 4>(ta, prows, n, d, a, st);
+    if (cl == 2) return launch_screen_t<SCR_KNN, SCR_KEEP, MET_L2, 2>(ta, prows, n, d, a, st);
+    return launch_screen_t<SCR_KNN, SCR_KEEP, MET_L2, 1>(ta, prows, n, d, a, st);
+  }
+  if (mode == SCR_KNN) return launch_screen_t<SCR_KNN, SCR_COLLECT, MET_L2, 1>(ta, prows, n, d, a, st);
+  return pass == SCR_KEEP ? launch_screen_t<SCR_DEP, SCR_KEEP, MET_L2, 1>(ta, prows, n, d, a, st)
+                          : launch_screen_t<SCR_DEP, SCR_COLLECT, MET_L2, 1>(ta, prows, n, d, a, st);
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -585,10 +685,12 @@ struct BfWs {
   float* ovf_thr;        // n
   int32_t* fb;           // n query ids for the exact SIMT kernels
   int32_t* counters;     // [0] overflowed rows, [1] SIMT rows
+  float* rkpad;          // dependent passes: rank keys, padded past n with NaN
 };
 
 size_t bf_ws_bytes(int64_t n, int d) {
-  return 2 * al256((size_t)n * d * 2) + al256((size_t)n * SC_KEEP * 4) + 9 * al256((size_t)n * 4) + 512;
+  return 2 * al256((size_t)n * d * 2) + al256((size_t)n * SC_KEEP * 4) + 9 * al256((size_t)n * 4) +
+         al256((size_t)SC_N * 4) + 512 + al256((size_t)(n + SC_N) * 4);
 }
 
 static BfWs carve_bf(void* ws, int64_t n, int d) {
@@ -603,7 +705,7 @@ static BfWs carve_bf(void* ws, int64_t n, int d) {
   w.qrows = (__nv_bfloat16*)take((size_t)n * d * 2);
   w.cand = (int32_t*)take((size_t)n * SC_KEEP * 4);
   w.nrm = (float*)take((size_t)n * 4);
-  w.nrm2 = (float*)take((size_t)n * 4);
+  w.nrm2 = (float*)take((size_t)(n + SC_N) * 4);  // padded: the screen reads whole 32-column chunks
   w.cnt = (int32_t*)take((size_t)n * 4);
   w.thr = (float*)take((size_t)n * 4);
   w.ovf = (int32_t*)take((size_t)n * 4);
@@ -612,6 +714,7 @@ static BfWs carve_bf(void* ws, int64_t n, int d) {
   w.fb = (int32_t*)take((size_t)n * 4);
   w.maxbits = (unsigned*)take((size_t)n * 4);
   w.counters = (int32_t*)take(256);
+  w.rkpad = (float*)take((size_t)(n + SC_N) * 4);
   return w;
 }
 
@@ -641,6 +744,8 @@ static cudaError_t prepare_rows(const DataView& fv, const BfWs& w, cudaStream_t 
   k_rows_to_bf16<<<blocks, 256, 0, st>>>(fv.X, fv.dtype, total, w.rows);
   note_launch();
   cudaError_t e = cudaMemsetAsync(w.maxbits, 0, 4, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.nrm2 + fv.n, 0, (size_t)SC_N * 4, st);  // the padding
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.counters, 0, 256, st);
   if (e != cudaSuccess) return e;
@@ -677,7 +782,7 @@ static pecann_status read_count(const int32_t* d_cnt, int32_t* h, cudaStream_t s
 // the exact re-rank on (query ids, candidates, counts, SC_CAP, rows); rows
 // beyond the capacity go to w.fb for the exact SIMT kernels.
 template <class DECIDE>
-static pecann_status collect_passes(int mode, const DataView& fv, const BfWs& w, const CUtensorMap& tp,
+static pecann_status collect_passes(int mode, const DataView& fv, const BfWs& w,
                                     const int32_t* qids_of_rows, const float* rank_key, int k, int64_t m, int* err,
                                     cudaStream_t st, DECIDE decide) {
   const int64_t batch = std::max<int64_t>(1, (fv.n * SC_KEEP) / SC_CAP);
@@ -700,7 +805,7 @@ static pecann_status collect_passes(int mode, const DataView& fv, const BfWs& w,
     a.cap = SC_CAP;
     a.out_ids = w.cand;
     a.out_cnt = w.cnt;
-    if ((s = cuda_status(launch_screen(mode, SCR_COLLECT, fv.metric, tq, tp, a, st), "brute-force collect pass")))
+    if ((s = cuda_status(launch_screen(mode, SCR_COLLECT, fv.metric, tq, w.rows, fv.n, fv.d, a, 1, st), "brute-force collect pass")))
       return s;
     k_collect_overflow<<<grid_for(mb), 256, 0, st>>>(w.cnt, mb, SC_CAP, w.ovf_ids, w.fb, w.counters + 1);
     note_launch();
@@ -716,9 +821,8 @@ pecann_status run_density_bf(const DataView& fv, const pecann_params* p, int32_t
   const BfWs w = carve_bf(bws, fv.n, fv.d);
   pecann_status s;
   if ((s = cuda_status(prepare_rows(fv, w, st), "brute-force index: rows"))) return s;
-  CUtensorMap tq, tp;
+  CUtensorMap tq;
   if ((s = cuda_status(make_map(&tq, w.rows, fv.n, fv.d, SC_M), "brute-force index"))) return s;
-  if ((s = cuda_status(make_map(&tp, w.rows, fv.n, fv.d, SC_N), "brute-force index"))) return s;
   ScreenArgs a = base_args(fv, w, err);
   a.nq = fv.n;
   a.k = p->k;
@@ -727,7 +831,7 @@ pecann_status run_density_bf(const DataView& fv, const pecann_params* p, int32_t
   a.out_thr = w.thr;
   a.ovf_list = w.ovf;
   a.ovf_cnt = w.counters + 0;
-  if ((s = cuda_status(launch_screen(SCR_KNN, SCR_KEEP, fv.metric, tq, tp, a, st), "brute-force screen"))) return s;
+  if ((s = cuda_status(launch_screen(SCR_KNN, SCR_KEEP, fv.metric, tq, w.rows, fv.n, fv.d, a, p->block_warps, st), "brute-force screen"))) return s;
   // exact decision for the complete rows (overflowed rows carry -1: skipped)
   cudaError_t e = launch_rerank_knn(fv, nullptr, fv.n, w.cand, w.cnt, SC_KEEP, p->k, knn_ids, knn_dist, rho, rkey,
                                     p->density, fb_list, fb_cnt, st);
@@ -739,7 +843,7 @@ pecann_status run_density_bf(const DataView& fv, const pecann_params* p, int32_t
                                          p->density, fb_list, fb_cnt, st),
                        "brute-force index: exact k-NN");
   };
-  if ((s = collect_passes(SCR_KNN, fv, w, tp, nullptr, nullptr, p->k, m, err, st, decide))) return s;
+  if ((s = collect_passes(SCR_KNN, fv, w, nullptr, nullptr, p->k, m, err, st, decide))) return s;
   // rows beyond the collect capacity join the fallback list of the caller
   int32_t m2 = 0;
   if ((s = read_count(w.counters + 1, &m2, st))) return s;
@@ -767,12 +871,17 @@ pecann_status run_dep_bf(const DataView& fv, const float* rank_key, const int32_
   const BfWs w = carve_bf(bws, fv.n, fv.d);
   pecann_status s;
   if ((s = cuda_status(prepare_rows(fv, w, st), "brute-force index: rows"))) return s;
+  // rank keys read four at a time by the screen: a copy padded with NaN
+  // (never ranked above anything)
+  cudaError_t e = cudaMemcpyAsync(w.rkpad, rank_key, (size_t)fv.n * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.rkpad + fv.n, 0xff, (size_t)SC_N * 4, st);
+  if ((s = cuda_status(e, "brute-force index: rank keys"))) return s;
+  rank_key = w.rkpad;
   k_gather_bf16<<<grid_for(nu * (fv.d / 8)), 256, 0, st>>>(w.rows, fv.d, U, nu, w.qrows);
   note_launch();
   if ((s = cuda_status(cudaGetLastError(), "brute-force index: gather"))) return s;
-  CUtensorMap tq, tp;
+  CUtensorMap tq;
   if ((s = cuda_status(make_map(&tq, w.qrows, nu, fv.d, SC_M), "brute-force index"))) return s;
-  if ((s = cuda_status(make_map(&tp, w.rows, fv.n, fv.d, SC_N), "brute-force index"))) return s;
   ScreenArgs a = base_args(fv, w, err);
   a.nq = nu;
   a.qids = U;
@@ -782,8 +891,8 @@ pecann_status run_dep_bf(const DataView& fv, const float* rank_key, const int32_
   a.out_thr = w.thr;
   a.ovf_list = w.ovf;
   a.ovf_cnt = w.counters + 0;
-  if ((s = cuda_status(launch_screen(SCR_DEP, SCR_KEEP, fv.metric, tq, tp, a, st), "brute-force screen"))) return s;
-  cudaError_t e = launch_rerank_dep(fv, U, nu, w.cand, w.cnt, SC_KEEP, lam, delta, st);
+  if ((s = cuda_status(launch_screen(SCR_DEP, SCR_KEEP, fv.metric, tq, w.rows, fv.n, fv.d, a, 1, st), "brute-force screen"))) return s;
+  e = launch_rerank_dep(fv, U, nu, w.cand, w.cnt, SC_KEEP, lam, delta, st);
   if ((s = cuda_status(e, "brute-force index: exact dependent points"))) return s;
   int32_t m = 0;
   if ((s = read_count(w.counters + 0, &m, st))) return s;
@@ -791,7 +900,7 @@ pecann_status run_dep_bf(const DataView& fv, const float* rank_key, const int32_
     return cuda_status(launch_rerank_dep(fv, ids, rows, cand, cnt, K, lam, delta, st),
                        "brute-force index: exact dependent points");
   };
-  if ((s = collect_passes(SCR_DEP, fv, w, tp, U, rank_key, 0, m, err, st, decide))) return s;
+  if ((s = collect_passes(SCR_DEP, fv, w, U, rank_key, 0, m, err, st, decide))) return s;
   int32_t m2 = 0;
   if ((s = read_count(w.counters + 1, &m2, st))) return s;
   if (m2 > 0) {

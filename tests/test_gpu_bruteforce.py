@@ -106,7 +106,7 @@ def test_small_n_and_exp_sum():
 
 def test_ties_overflow_the_kept_list():
     """Coarse uint8 values: thousands of points at equal distances, so the
-    band around the k-th key holds more than the 64 kept candidates. Those
+    band around the k-th key holds more than the 80 kept candidates. Those
     points take the collect pass (up to 1,024 candidates) or, beyond it, the
     exact SIMT kernels; the results are still the oracle's, ties broken by id."""
     X, _ = synth.u8_mixture(n=4000, d=64, components=4, seed=208)

@@ -136,6 +136,18 @@ def test_cluster_sweep_matches_single_calls_and_oracle():
                            n_clusters=st.get("n_clusters", 1))
             l1, n1 = pc.pecann_cluster(dens["density"], dep["dep"], dep["dep_dist"], p1)
             assert torch.equal(l1, labels[i]) and n1 == counts[i]
+    # all settings run in shared passes: the sweep's kernel count does not
+    # grow with the number of settings (9 settings, then 27 with repeats)
+    l0 = pc.pecann_kernel_launches()
+    pc.pecann_cluster_sweep(dens["density"], dep["dep"], dep["dep_dist"], settings,
+                            knn_ids=dens["knn_ids"], rank_key=dens["rank_key"])
+    l1 = pc.pecann_kernel_launches()
+    labels3, counts3 = pc.pecann_cluster_sweep(dens["density"], dep["dep"], dep["dep_dist"], settings * 3,
+                                               knn_ids=dens["knn_ids"], rank_key=dens["rank_key"])
+    l2 = pc.pecann_kernel_launches()
+    assert l2 - l1 == l1 - l0
+    assert torch.equal(labels3[: len(settings)], labels) and torch.equal(labels3[len(settings):2 * len(settings)], labels)
+    assert counts3[: len(settings)] == counts
     # the local center needs the k-NN lists in the single-setting call
     with pytest.raises(pc.PecannError) as e:
         pc.pecann_cluster(dens["density"], dep["dep"], dep["dep_dist"], pc.params(center=pc.CENTER_LOCAL))
