@@ -69,6 +69,8 @@ def _load():
         _lib.orc_knn_density_rows.argtypes = [P, vp, i32, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp,
                                               ctypes.c_int]
         _lib.orc_knn_density_rows.restype = ctypes.c_int
+        _lib.orc_nndescent.argtypes = [P, i32, i32, vp, i32, f32, i32, vp, vp, vp, ctypes.c_int]
+        _lib.orc_nndescent.restype = ctypes.c_int
         _lib.orc_dependent_points.argtypes = [P, vp, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp,
                                               ctypes.c_int]
         _lib.orc_dependent_points.restype = ctypes.c_int
@@ -187,6 +189,24 @@ def knn_density_rows(P: Points, G, rows, L: int, k: int, density: int = DENS_KTH
     if rc:
         raise ValueError("orc_knn_density_rows: bad arguments")
     return dict(ids=ids, dist=dist, rho=rho, key=key, fallback=fb)
+
+
+def nndescent(P: Points, K: int, init: np.ndarray, rounds: int, alpha: float, R: int, threads: int | None = None):
+    """NN-Descent graph index (the paper's PyNNDescent option, Sec. 5.1):
+    synchronous rounds from the given initial lists (repeats x n x K), the
+    repeats merged, then RobustPrune and reverse edges. Returns dict knn (n,K)
+    int32, G (n,R) int32, changes (repeats, rounds) int64."""
+    init = np.ascontiguousarray(init, dtype=np.int32)
+    repeats = init.shape[0]
+    n = P.n
+    knn = np.empty((n, K), np.int32)
+    G = np.empty((n, R), np.int32)
+    ch = np.zeros((repeats, max(rounds, 1)), np.int64)
+    rc = _load().orc_nndescent(P.ptr, K, repeats, _p(init), rounds, alpha, R, _p(knn), _p(G), _p(ch),
+                               threads or default_threads())
+    if rc:
+        raise ValueError("orc_nndescent: bad arguments")
+    return dict(knn=knn, G=G, changes=ch[:, :rounds])
 
 
 def dependent_points(P: Points, G: np.ndarray, key: np.ndarray, knn_ids: np.ndarray, Ld: int,

@@ -1039,3 +1039,224 @@ int orc_build_graph(const orc_points* P, int32_t R, int32_t L, float alpha, cons
   free(ws);
   return 0;
 }
+
+/* ---------- NN-Descent graph index (Sec. 5.1, graph indices) ---------- */
+
+/* One list per point: K (dis, id) items sorted ascending. */
+static void sort_unique_top(item* a, int64_t* m, int32_t K) {
+  qsort(a, (size_t)*m, sizeof(item), item_cmp);
+  int64_t w = 0;
+  for (int64_t t = 0; t < *m; t++) /* the same id has the same dis: adjacent */
+    if (w == 0 || a[w - 1].id != a[t].id) a[w++] = a[t];
+  *m = w < K ? w : K;
+}
+
+typedef struct {
+  const orc_points* P;
+  int32_t K;
+  const int32_t* N;     /* n x K ids of the snapshot */
+  const float* Nd;      /* n x K dis */
+  const int32_t* Rv;    /* n x K reverse ids (-1 padded) */
+  int32_t* N2;          /* n x K new ids */
+  float* N2d;
+  int64_t* changed;     /* per point: 1 when the list changed */
+} nnd_ctx;
+
+/* C(x) = N(x) u R(x), the valid ids */
+static int32_t nnd_neigh(const nnd_ctx* x, int64_t p, int32_t* out) {
+  int32_t m = 0;
+  for (int32_t t = 0; t < x->K; t++) out[m++] = x->N[p * x->K + t];
+  for (int32_t t = 0; t < x->K; t++)
+    if (x->Rv[p * x->K + t] >= 0) out[m++] = x->Rv[p * x->K + t];
+  return m;
+}
+
+static void nnd_round_body(void* c, int64_t u, int tid) {
+  (void)tid;
+  const nnd_ctx* x = (const nnd_ctx*)c;
+  const int32_t K = x->K;
+  int32_t* cu = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)K);
+  int32_t* cp = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)K);
+  const int32_t mu = nnd_neigh(x, u, cu);
+  /* candidates: N(u), C(u), and C(p) for every p in C(u); u itself excluded */
+  int64_t cap = (int64_t)K + mu + (int64_t)mu * 2 * K;
+  item* a = (item*)malloc(sizeof(item) * (size_t)cap);
+  int64_t m = 0;
+  for (int32_t t = 0; t < K; t++) {
+    a[m].id = x->N[u * K + t];
+    a[m].dis = x->Nd[u * K + t];
+    m++;
+  }
+  for (int32_t s = 0; s < mu; s++) {
+    const int32_t p = cu[s];
+    if (p != u) {
+      a[m].id = p;
+      a[m].dis = orc_dis(x->P, u, p);
+      m++;
+    }
+    const int32_t mp = nnd_neigh(x, p, cp);
+    for (int32_t t = 0; t < mp; t++) {
+      const int32_t v = cp[t];
+      if (v == u) continue;
+      a[m].id = v;
+      a[m].dis = orc_dis(x->P, u, v);
+      m++;
+    }
+  }
+  sort_unique_top(a, &m, K);
+  int64_t diff = 0;
+  for (int32_t t = 0; t < K; t++) {
+    x->N2[u * K + t] = a[t].id;
+    x->N2d[u * K + t] = a[t].dis;
+    diff |= a[t].id != x->N[u * K + t];
+  }
+  x->changed[u] = diff;
+  free(a);
+  free(cp);
+  free(cu);
+}
+
+/* Reverse lists of the snapshot: Rv(x) = the K smallest (dis, q) among the
+   q with x in N(q); -1 padded. */
+static void nnd_reverse(int64_t n, int32_t K, const int32_t* N, const float* Nd, int32_t* Rv) {
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t q = 0; q < n; q++)
+    for (int32_t t = 0; t < K; t++) cnt[N[q * K + t] + 1]++;
+  for (int64_t x = 0; x < n; x++) cnt[x + 1] += cnt[x];
+  item* e = (item*)malloc(sizeof(item) * (size_t)(n * K > 0 ? n * K : 1));
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t x = 0; x < n; x++) pos[x] = cnt[x];
+  for (int64_t q = 0; q < n; q++)
+    for (int32_t t = 0; t < K; t++) {
+      const int32_t x = N[q * K + t];
+      e[pos[x]].id = (int32_t)q;
+      e[pos[x]].dis = Nd[q * K + t];
+      pos[x]++;
+    }
+  for (int64_t x = 0; x < n; x++) {
+    item* seg = e + cnt[x];
+    int64_t m = cnt[x + 1] - cnt[x];
+    qsort(seg, (size_t)m, sizeof(item), item_cmp);
+    for (int32_t t = 0; t < K; t++) Rv[x * K + t] = t < m ? seg[t].id : -1;
+  }
+  free(pos);
+  free(e);
+  free(cnt);
+}
+
+/*
+ * NN-Descent graph index. The paper's framework offers PyNNDescent (and
+ * HCNNG) graphs with a num_repeats argument (Sec. 5.1, graph indices) but
+ * prints no steps; this follows NN-Descent (Dong et al., "Efficient k-nearest
+ * neighbor graph construction for generic similarity measures") in a
+ * synchronous form, every new list computed from the same snapshot:
+ *   for each repeat r: N(u) <- the K ids init[r][u] sorted by (dis, id);
+ *     repeat `rounds` times or until no list changes:
+ *       R(x) <- the K smallest (D(q, x), q) among the q with x in N(q);
+ *       C(x) <- N(x) u R(x);
+ *       N'(u) <- the K smallest (dis, id) of N(u) u C(u) u (U_{p in C(u)} C(p)), minus u;
+ *   the repeats are merged: N(u) <- the K smallest of the union of their lists;
+ *   G(u) <- RobustPrune(u, N(u), alpha, R); then every edge u -> y gives y the
+ *   source u, all points as one batch of the Vamana build's reverse step
+ *   (sources in id order, appended when they fit, else RobustPrune(y, ...)).
+ * init: repeats x n x K ids (distinct, none equal to its point). Outputs knn
+ * (n x K ids, sorted by (dis, id)), G (n x R, -1 padded) and changes
+ * (repeats x rounds: the lists that changed in each round, 0 after
+ * convergence). Returns 0, or 1 on bad arguments.
+ */
+int orc_nndescent(const orc_points* P, int32_t K, int32_t repeats, const int32_t* init, int32_t rounds,
+                  float alpha, int32_t R, int32_t* knn, int32_t* G, int64_t* changes, int nthreads) {
+  const int64_t n = P->n;
+  if (K < 1 || K >= n || repeats < 1 || rounds < 0 || R < 1) return 1;
+  if (nthreads < 1) nthreads = 1;
+  int32_t* N = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * K));
+  float* Nd = (float*)malloc(sizeof(float) * (size_t)(n * K));
+  int32_t* N2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * K));
+  float* N2d = (float*)malloc(sizeof(float) * (size_t)(n * K));
+  int32_t* Rv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * K));
+  int64_t* changed = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  item* all = (item*)malloc(sizeof(item) * (size_t)(n * K * repeats));
+  int64_t* nall = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+  item* tmp = (item*)malloc(sizeof(item) * (size_t)K);
+  for (int64_t i = 0; i < (int64_t)repeats * rounds; i++) changes[i] = 0;
+  for (int32_t r = 0; r < repeats; r++) {
+    for (int64_t u = 0; u < n; u++) {
+      for (int32_t t = 0; t < K; t++) {
+        tmp[t].id = init[((int64_t)r * n + u) * K + t];
+        tmp[t].dis = orc_dis(P, u, tmp[t].id);
+      }
+      qsort(tmp, (size_t)K, sizeof(item), item_cmp);
+      for (int32_t t = 0; t < K; t++) {
+        N[u * K + t] = tmp[t].id;
+        Nd[u * K + t] = tmp[t].dis;
+      }
+    }
+    for (int32_t it = 0; it < rounds; it++) {
+      nnd_reverse(n, K, N, Nd, Rv);
+      nnd_ctx c = {P, K, N, Nd, Rv, N2, N2d, changed};
+      parallel_for(n, nthreads, nnd_round_body, &c);
+      int64_t ch = 0;
+      for (int64_t u = 0; u < n; u++) ch += changed[u];
+      changes[(int64_t)r * rounds + it] = ch;
+      memcpy(N, N2, sizeof(int32_t) * (size_t)(n * K));
+      memcpy(Nd, N2d, sizeof(float) * (size_t)(n * K));
+      if (ch == 0) break;
+    }
+    for (int64_t u = 0; u < n; u++)
+      for (int32_t t = 0; t < K; t++) {
+        item* d = &all[(u * repeats + r) * K + t];
+        d->id = N[u * K + t];
+        d->dis = Nd[u * K + t];
+      }
+  }
+  /* merge the repeats, then prune */
+  for (int64_t i = 0; i < n * R; i++) G[i] = -1;
+  int32_t* out = (int32_t*)malloc(sizeof(int32_t) * (size_t)R);
+  for (int64_t u = 0; u < n; u++) {
+    item* seg = all + u * repeats * K;
+    int64_t m = (int64_t)repeats * K;
+    sort_unique_top(seg, &m, K);
+    for (int32_t t = 0; t < K; t++) knn[u * K + t] = seg[t].id;
+    int32_t deg = robust_prune(P, u, seg, m, alpha, R, out);
+    for (int32_t t = 0; t < deg; t++) G[u * R + t] = out[t];
+  }
+  free(out);
+  /* reverse edges, all points as one batch, grouped by target */
+  int64_t np = 0;
+  int32_t* pairs = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)(n * R > 0 ? n * R : 1));
+  int64_t* tgt_begin = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n * R + 1));
+  for (int64_t u = 0; u < n; u++)
+    for (int32_t t = 0; t < R; t++) {
+      const int32_t y = G[u * R + t];
+      if (y < 0) break;
+      pairs[2 * np] = y;
+      pairs[2 * np + 1] = (int32_t)u;
+      np++;
+    }
+  qsort(pairs, (size_t)np, 2 * sizeof(int32_t), pair_cmp);
+  int64_t ng = 0;
+  for (int64_t e = 0; e < np; e++)
+    if (e == 0 || pairs[2 * e] != pairs[2 * (e - 1)]) tgt_begin[ng++] = e;
+  tgt_begin[ng] = np;
+  build_ctx bc;
+  memset(&bc, 0, sizeof(bc));
+  bc.P = P;
+  bc.G = G;
+  bc.R = R;
+  bc.alpha = alpha;
+  bc.tgt_begin = tgt_begin;
+  bc.pairs = pairs;
+  parallel_for(ng, nthreads, build_reverse_body, &bc);
+  free(tgt_begin);
+  free(pairs);
+  free(tmp);
+  free(nall);
+  free(all);
+  free(changed);
+  free(Rv);
+  free(N2d);
+  free(N2);
+  free(Nd);
+  free(N);
+  return 0;
+}

@@ -141,6 +141,32 @@ def batched_sets(count: int = 64, n_lo: int = 2_000, n_hi: int = 200_000, dims=(
     return out
 
 
+def random_neighbours(n: int, K: int, repeats: int = 1, seed: int = SEED_BASE + 19) -> np.ndarray:
+    """Initial neighbour lists of an NN-Descent build: for every repeat and
+    point, K distinct ids drawn uniformly from the other n - 1 points.
+    Returns int32 (repeats, n, K)."""
+    if not 1 <= K < n:
+        raise ValueError("need 1 <= K < n")
+    g = rng(seed)
+    out = np.empty((repeats, n, K), np.int32)
+    rows = np.arange(n)[:, None]
+    for r in range(repeats):
+        draw = g.integers(0, n - 1, size=(n, 2 * K))
+        draw = np.where(draw >= rows, draw + 1, draw)  # skip the point itself
+        srt = np.sort(draw, axis=1)
+        first = np.ones_like(srt, dtype=bool)
+        first[:, 1:] = srt[:, 1:] != srt[:, :-1]
+        # the K smallest distinct draws of each row (rows short of K are redrawn below)
+        order = np.argsort(~first, axis=1, kind="stable")
+        pick = np.take_along_axis(srt, order, 1)[:, :K]
+        short = np.flatnonzero(first.sum(1) < K)
+        for i in short:
+            choice = g.choice(n - 1, size=K, replace=False)
+            pick[i] = np.where(choice >= i, choice + 1, choice)
+        out[r] = pick
+    return out
+
+
 def insertion_order(n: int, seed: int = SEED_BASE + 17) -> np.ndarray:
     """Random insertion permutation for the graph build (int32)."""
     return rng(seed).permutation(n).astype(np.int32)

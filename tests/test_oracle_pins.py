@@ -607,3 +607,74 @@ def test_exact_knn_queries_and_recall():
     assert exact.knn_recall(np.array([[1.0, 2.0, 5.0, 6.0]]), ex) == 0.5
     assert exact.knn_recall(np.array([[1.0, 2.0, 3.0, 4.0 * (1 + 5e-6)]]), ex) == 1.0
     assert exact.knn_recall(np.array([[1.0, 2.0, 3.0, 4.0 * (1 + 5e-5)]]), ex) == 0.75
+
+
+# ---------------------------------------------------------------- NN-Descent graph index
+
+def _nnd_rounds_python(X, init, rounds):
+    """Synchronous NN-Descent rounds restated with Python sets on integer
+    data (squared distances exact): R(x) = the K smallest (d, q) with x in
+    N(q); C(x) = N(x) | R(x); N'(u) = the K smallest (d, id) of
+    N(u) | C(u) | union of C(p) for p in C(u), without u."""
+    n, K = init.shape
+    d2 = lambda a, b: int(((X[a].astype(np.int64) - X[b].astype(np.int64)) ** 2).sum())
+    N = [sorted(init[u].tolist(), key=lambda v: (d2(u, v), v)) for u in range(n)]
+    for _ in range(rounds):
+        rev = {x: [] for x in range(n)}
+        for q in range(n):
+            for x in N[q]:
+                rev[x].append(q)
+        Rv = {x: sorted(rev[x], key=lambda q: (d2(q, x), q))[:K] for x in range(n)}
+        C = {x: set(N[x]) | set(Rv[x]) for x in range(n)}
+        new = []
+        for u in range(n):
+            cand = set(N[u]) | C[u]
+            for p in C[u]:
+                cand |= C[p]
+            cand.discard(u)
+            new.append(sorted(cand, key=lambda v: (d2(u, v), v))[:K])
+        N = new
+    return np.array(N, np.int32)
+
+
+def test_nndescent_rounds_match_a_set_restatement():
+    g = np.random.default_rng(21)
+    X = g.integers(0, 6, size=(40, 4)).astype(np.float32)  # coarse: many equal distances, ties by id
+    init = synth.random_neighbours(40, 5, repeats=1, seed=22)
+    P = oracle.Points(X)
+    for rounds in (1, 3):
+        r = oracle.nndescent(P, 5, init, rounds=rounds, alpha=1.2, R=8)
+        assert (r["knn"] == _nnd_rounds_python(X, init[0], rounds)).all(), rounds
+
+
+def test_nndescent_exact_lists_are_a_fixed_point_and_repeats_merge():
+    X, _ = _mixture(600, 16, 5, np.random.default_rng(23))
+    P = oracle.Points(X)
+    ei, _ = exact.exact_knn(X, 8)
+    r = oracle.nndescent(P, 8, ei[None].astype(np.int32), rounds=3, alpha=1.2, R=12)
+    assert r["changes"][0, 0] == 0 and (r["knn"] == ei).all()
+    # two repeats = the 8 smallest of the union of the two single-repeat lists
+    init = synth.random_neighbours(600, 8, repeats=2, seed=24)
+    a = oracle.nndescent(P, 8, init[:1], rounds=2, alpha=1.2, R=12)["knn"]
+    b = oracle.nndescent(P, 8, init[1:], rounds=2, alpha=1.2, R=12)["knn"]
+    both = oracle.nndescent(P, 8, init, rounds=2, alpha=1.2, R=12)["knn"]
+    for u in range(600):
+        cand = sorted(set(a[u]) | set(b[u]), key=lambda v: (oracle.dis(P, u, int(v)), v))[:8]
+        assert list(both[u]) == cand, u
+
+
+def test_nndescent_graph_invariants_and_recall():
+    X, _ = _mixture(3000, 32, 8, np.random.default_rng(25))
+    P = oracle.Points(X)
+    r = oracle.nndescent(P, 16, synth.random_neighbours(3000, 16, repeats=2, seed=26), rounds=12, alpha=1.2, R=24)
+    ch = r["changes"]
+    assert (ch[:, -1] == 0).all()  # converged within 12 rounds
+    _, ed = exact.exact_knn(X, 16)
+    got = np.array([[np.sqrt(oracle.dis(P, u, int(v))) for v in r["knn"][u]] for u in range(3000)])
+    assert exact.knn_recall(got, ed) >= 0.95
+    G = r["G"]
+    deg = (G >= 0).sum(1)
+    assert deg.max() <= 24 and deg.min() >= 1
+    for u in range(3000):
+        row = G[u][: deg[u]]
+        assert (G[u][deg[u]:] == -1).all() and u not in row and len(set(row.tolist())) == len(row)
