@@ -67,8 +67,9 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="headline only: no variants, recall, e2e or CPU baseline")
     ap.add_argument("--variant-steps", type=int, default=2, help="timed steps of each report line")
-    ap.add_argument("--workload", default="vmf1024", choices=["vmf1024", "u8-1m", "batched64", "sphere384"],
-                    help="vmf1024: the benchmark line (with its variants); u8-1m: the uint8 graph line alone")
+    ap.add_argument("--workload", default="vmf1024",
+                    choices=["vmf1024", "vmf1024-graph", "u8-1m", "batched64", "sphere384"],
+                    help="vmf1024: the benchmark line (with its variants); vmf1024-graph / u8-1m: report lines alone")
     return ap.parse_args()
 
 
@@ -279,7 +280,9 @@ class Path:
         if dens_events is not None:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
+        torch.cuda.nvtx.range_push("pecann_density")
         pc.pecann_density(ds, G, self.p, ws=self.ws, out=self.dens)
+        torch.cuda.nvtx.range_pop()
         if dens_events is not None:
             b.record()
             dens_events.append((a, b))
@@ -612,6 +615,35 @@ def u8_variants(args, dev, stream, threads):
     return out
 
 
+def run_vmf_graph_only(args):
+    """The 1.28M x 1024 rows on the Vamana graph alone (report lines), recall
+    judged against the exact index run once, untimed."""
+    import torch
+
+    from paper_2312_03940_gb300 import build as pbuild
+    from paper_2312_03940_gb300 import pecann as pc
+
+    pbuild.build()
+    pc.load_library()
+    import oracle
+
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    n = args.n or VMF["n"]
+    X, _ = vmf_data(n)
+    Xd = torch.from_numpy(X).to(dev)
+    p = pc.params(k=VMF["k"], L_search=VMF["L"], center=pc.CENTER_PRODUCT, n_clusters=VMF["n_clusters"],
+                  index=pc.INDEX_BRUTE_FORCE)
+    ref = Path(pc.Dataset(Xd, metric=pc.IP), None, p, dev)
+    ref.step(None)
+    ex_dist, ex_labels = ref.dens["knn_dist"].cpu().numpy(), ref.labels.cpu().numpy()
+    del ref
+    torch.cuda.empty_cache()
+    out = vmf_graph_variants(args, X, Xd, ex_dist, ex_labels, dev, torch.cuda.current_stream(),
+                             oracle.default_threads())
+    print(json.dumps({"workload": "vmf1024-graph", "lines": out}), flush=True)
+
+
 def run_u8_only(args):
     """The uint8 workload alone on its graph and on the exact index (report)."""
     import torch
@@ -793,6 +825,8 @@ def main():
         run_reduced(args, "sphere384")
     elif args.workload == "u8-1m":
         run_u8_only(args)
+    elif args.workload == "vmf1024-graph":
+        run_vmf_graph_only(args)
     else:
         run_ours(args)
 

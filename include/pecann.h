@@ -17,20 +17,23 @@
  *    aligned, of at least pecann_workspace_size() bytes. Its contents on entry
  *    do not matter; on return they are undefined.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
- *    queued on it. pecann_search, pecann_build_graph, pecann_density,
- *    pecann_density_noalloc and pecann_dependent_points return only after
- *    their work on `stream` has finished (they read back an error word or
- *    small counters); the other calls are asynchronous unless a host output
- *    is requested.
+ *    queued on it. pecann_search, pecann_build_graph, pecann_build_nndescent,
+ *    pecann_density, pecann_density_noalloc and pecann_dependent_points
+ *    return only after their work on `stream` has finished (they read back
+ *    an error word or small counters); the other calls are asynchronous
+ *    unless a host output is requested.
  *  - Errors are returned as pecann_status; nothing is thrown across the ABI.
  *    PECANN_EINVAL: an argument is out of range (checked on the host before
  *    any GPU work); PECANN_ENOMEM: ws_bytes is too small; PECANN_ECUDA: a
  *    CUDA call failed (the message is available from pecann_last_error());
  *    PECANN_EUNSUPPORTED: a valid combination this build has no kernel for;
  *    PECANN_EINTERNAL: a kernel detected an inconsistency (e.g. a graph entry
- *    out of range) and skipped the offending access. PECANN_ETIMEOUT is
- *    reserved: no kernel of this library waits on another (the batched
- *    form's work queue is a fetch-and-add counter), so no call returns it.
+ *    out of range) and skipped the offending access. PECANN_ETIMEOUT: a
+ *    brute-force screen (PECANN_INDEX_BRUTE_FORCE) gave up waiting on one of
+ *    its own pipeline barriers after 2 s; every kernel thread stops, frees
+ *    its tensor memory and returns, so the context stays usable. No other
+ *    kernel waits on another (the batched form's work queue is a
+ *    fetch-and-add counter).
  *  - Point rows are n x d, row-major, contiguous, 16-byte aligned. d must be
  *    a multiple of 4 (FP32), 8 (BF16) or 16 (U8, FP8). U8 supports the L2
  *    metric with d <= 256 (so that every distance is an exact integer in FP32).
@@ -225,6 +228,40 @@ PECANN_API pecann_status pecann_search(const pecann_dataset* ds, const int32_t* 
 PECANN_API pecann_status pecann_build_graph(const pecann_dataset* ds, const pecann_params* p,
                                  const int32_t* d_order, int32_t* d_graph, int32_t* d_degree,
                                  void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * NN-Descent graph index (Sec. 5.1, graph indices: the framework also builds
+ * its graph with PyNNDescent, repeated num_repeats times). The paper prints
+ * no steps for it; the library follows NN-Descent (Dong, Charikar and Li,
+ * 2011) in a synchronous form, so that results do not depend on thread
+ * order:
+ *   for each repeat r: N(u) <- the K ids d_init[r][u] sorted by (dis, id);
+ *     each round, from one snapshot of every list:
+ *       R(x) <- the K smallest (dis(q, x), q) over the q with x in N(q);
+ *       C(x) <- N(x) u R(x);
+ *       N'(u) <- the K smallest (dis, id) of N(u) u C(u) u U_{p in C(u)} C(p),
+ *                u itself left out;
+ *     until no list changes or after `rounds` rounds;
+ *   the repeats are merged: N(u) <- the K smallest of the union of their lists;
+ *   G(u) <- RobustPrune(u, N(u), alpha, R); then every edge u -> y adds u to
+ *   y as the reverse step of pecann_build_graph does for one batch holding
+ *   all points (sources in id order; y re-pruned when its degree would
+ *   exceed R).
+ * d_init: repeats x n x K int32, each list K distinct ids in [0, n) other
+ * than its point (a list that breaks this is reported as PECANN_EINTERNAL).
+ * 1 <= K <= min(64, n - 1), 1 <= repeats <= 64, 0 <= rounds <= 1000; reads
+ * p->R and p->alpha. FP32 (or uint8) rows: BF16 / FP8 datasets use data_f32.
+ * Outputs: d_graph (n x R, -1 padded); d_degree (n, may be NULL); d_knn
+ * (device n x K, may be NULL): the merged lists, ascending by (dis, id);
+ * h_changes (HOST, repeats x rounds int64, may be NULL): how many lists each
+ * round changed (0 for rounds not run after convergence). Blocks until done.
+ */
+PECANN_API pecann_status pecann_nndescent_workspace_size(const pecann_dataset* ds, const pecann_params* p,
+                                                         int32_t K, int32_t repeats, size_t* bytes);
+PECANN_API pecann_status pecann_build_nndescent(const pecann_dataset* ds, const pecann_params* p, int32_t K,
+                                                int32_t repeats, const int32_t* d_init, int32_t rounds,
+                                                int32_t* d_graph, int32_t* d_degree, int32_t* d_knn,
+                                                int64_t* h_changes, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * k nearest neighbours and density of every point (Algorithm 2 lines 2-4).

@@ -20,8 +20,12 @@
  *   orc_robust_prune      RobustPrune(alpha, R) of Vamana (Sec. 3.2 defers it
  *                         to DiskANN; the published DiskANN rule is used)
  *   orc_build_graph       Vamana batched construction (Sec. 3.2, Sec. 4.1)
+ *   orc_nndescent         NN-Descent graph index (Sec. 5.1, graph indices; the
+ *                         paper names it without steps: synchronous rounds of
+ *                         Dong et al.'s method, see its own comment)
+ *   orc_knn_density_rows  Algorithm 2 lines 2-4 for a list of points only
  *
- * Readings of points the paper leaves open (each is listed in the design notes):
+ * Where the paper leaves a point open, this file takes the readings below:
  *  - Canonical FP32 dissimilarity. For rows a, b of d elements (d % 4 == 0) 32
  *    partial sums s[0..31] start at +0. Chunk c (elements 4c..4c+3) is owned by
  *    partial c % 32; chunks are taken in ascending c and, inside a chunk, in

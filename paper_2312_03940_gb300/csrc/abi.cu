@@ -469,6 +469,55 @@ pecann_status pecann_build_graph(const pecann_dataset* ds, const pecann_params* 
   return read_err(&h->err, st);
 }
 
+static pecann_status check_nndescent(const DataView& dv, const pecann_params* p, int32_t K, int32_t repeats,
+                                     int32_t rounds) {
+  if (K < 1 || K > 64 || K >= dv.n) return set_last_error("K must be in 1..min(64, n - 1)"), PECANN_EINVAL;
+  if (repeats < 1 || repeats > 64) return set_last_error("repeats must be in 1..64"), PECANN_EINVAL;
+  if (rounds < 0 || rounds > 1000) return set_last_error("rounds must be in 0..1000"), PECANN_EINVAL;
+  if (p->R < 1 || p->R > 256) return set_last_error("R must be in 1..256"), PECANN_EINVAL;
+  if (!(p->alpha >= 1.0f)) return set_last_error("alpha must be >= 1"), PECANN_EINVAL;
+  return PECANN_OK;
+}
+
+pecann_status pecann_nndescent_workspace_size(const pecann_dataset* ds, const pecann_params* p, int32_t K,
+                                              int32_t repeats, size_t* bytes) {
+  DataView dv0, dv;
+  pecann_status s = check_dataset(ds, &dv0, &dv);
+  if (s) return s;
+  if (!p || !bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
+  if ((s = check_nndescent(dv, p, K, repeats, 0))) return s;
+  *bytes = HDR + nndescent_ws_bytes(dv.n, K, repeats, p->R);
+  return PECANN_OK;
+}
+
+pecann_status pecann_build_nndescent(const pecann_dataset* ds, const pecann_params* p, int32_t K, int32_t repeats,
+                                     const int32_t* d_init, int32_t rounds, int32_t* d_graph, int32_t* d_degree,
+                                     int32_t* d_knn, int64_t* h_changes, void* ws, size_t ws_bytes, void* stream) {
+  DataView dv0, dv;
+  pecann_status s = check_dataset(ds, &dv0, &dv);  // FP32 (or U8) rows, like the Vamana build
+  if (s) return s;
+  if (!p || !d_init || !d_graph || !ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if ((s = check_nndescent(dv, p, K, repeats, rounds))) return s;
+  if (ws_bytes < HDR + nndescent_ws_bytes(dv.n, K, repeats, p->R))
+    return set_last_error("workspace too small"), PECANN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* h = (WsHeader*)ws;
+  cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  if (h_changes)
+    for (int64_t i = 0; i < (int64_t)repeats * rounds; i++) h_changes[i] = 0;
+  e = run_nndescent(dv, K, repeats, d_init, rounds, p->alpha, p->R, d_graph, d_knn, h_changes, (uint8_t*)ws + HDR,
+                    &h->err, st);
+  if ((s = cuda_status(e, "nn-descent"))) return s;
+  if (d_degree) {
+    k_degree<<<(unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8), 256, 0, st>>>(
+        dv.n, p->R, d_graph, d_degree);
+    note_launch();
+    if ((s = cuda_status(cudaGetLastError(), "degree"))) return s;
+  }
+  return read_err(&h->err, st);
+}
+
 pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, const pecann_params* p,
                              int32_t* d_knn_ids, float* d_knn_dist, float* d_density, float* d_rank_key,
                              void* ws, size_t ws_bytes, void* stream) {

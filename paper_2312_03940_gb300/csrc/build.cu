@@ -409,6 +409,140 @@ int64_t batch_cap_of(int64_t n, float frac) {
   return cap < 1 ? 1 : cap;
 }
 
+// Steps 2 and 3 for the m points of b.batch, whose candidate lists are
+// b.vis_ids / b.vis_dis / b.vis_cnt: prune each point's out-list, then apply
+// the reverse edges grouped by target. b.cnt and b.fillc are zero on entry
+// and on return.
+static cudaError_t prune_reverse_batch(const DataView& dv, BuildArgs& b, int64_t m, int32_t* counters,
+                                       cudaStream_t st) {
+  const int R = b.R;
+  const size_t new_smem_warp = (size_t)b.cap_new * 12 + (size_t)R * 8;
+  const int new_wpb = new_smem_warp * 4 <= 200 * 1024 ? 4 : (new_smem_warp * 2 <= 200 * 1024 ? 2 : 1);
+  const size_t rev_smem_warp = (size_t)PRUNE_CAP * 16 + (size_t)R * 4;
+  const int rev_wpb = 2;
+  const int sms = num_sms();
+  return dispatch_layout(dv, [&](auto dt, auto met, auto wv, auto cpl) -> cudaError_t {
+      constexpr int DT = decltype(dt)::value, MET = decltype(met)::value;
+      constexpr int W = decltype(wv)::value, CPL = decltype(cpl)::value;
+      auto kn = k_prune_new<DT, MET, W, CPL>;
+      size_t sm = new_smem_warp * new_wpb;
+      set_where("build: prune attribute");
+      cudaError_t ee = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (ee != cudaSuccess) return ee;
+      set_where("build: prune launch");
+      int64_t blocks = std::min<int64_t>((m + new_wpb - 1) / new_wpb, (int64_t)sms * 8);
+      kn<<<(unsigned)blocks, new_wpb * 32, sm, st>>>(b); note_launch();
+      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+      set_where("build: reverse-edge counters");
+      if ((ee = cudaMemsetAsync(counters, 0, 64, st)) != cudaSuccess) return ee;
+      int64_t edges = m * R;
+      unsigned eb = (unsigned)std::min<int64_t>((edges + 255) / 256, (int64_t)sms * 16);
+      set_where("build: reverse-edge count");
+      k_rev_count<<<eb, 256, 0, st>>>(b); note_launch();
+      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+      set_where("build: reverse-edge offsets");
+      k_rev_offsets<<<eb, 256, 0, st>>>(b); note_launch();
+      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+      set_where("build: reverse-edge fill");
+      k_rev_fill<<<eb, 256, 0, st>>>(b); note_launch();
+      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+      auto ka = k_rev_apply<DT, MET, W, CPL>;
+      size_t sm2 = rev_smem_warp * rev_wpb;
+      set_where("build: reverse-edge apply");
+      if ((ee = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
+        return ee;
+      unsigned ab = (unsigned)std::min<int64_t>((edges + rev_wpb - 1) / rev_wpb, (int64_t)sms * 8);
+      ka<<<ab, rev_wpb * 32, sm2, st>>>(b); note_launch();
+      k_rev_apply_big<DT, MET, W, CPL><<<BIG_WARPS, 32, 0, st>>>(b); note_launch();
+      return cudaGetLastError();
+    });
+}
+
+__global__ void k_iota_fill(int64_t n, int32_t* iota, int32_t* cnt, int32_t k) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    iota[i] = (int32_t)i;
+    cnt[i] = k;
+  }
+}
+
+static size_t pow2_size(size_t x) {
+  size_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+size_t all_prune_ws_bytes(int64_t n, int R) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t big_cap = pow2_size((size_t)n + R);
+  return 5 * al((size_t)n * 4) + 3 * al((size_t)n * R * 4) + al(64) + 2 * al((size_t)BIG_WARPS * big_cap * 8);
+}
+
+// Steps 2 and 3 of a batch that holds every point, from given candidate
+// lists (ids / dis: n x K, sorted by (dis, id), unique) on an empty graph:
+// G(p) <- RobustPrune(p, list(p), alpha, R), then the reverse edges of all
+// points grouped by target. Used by graph indices built without searches.
+cudaError_t run_all_prune(const DataView& dv, int R, float alpha, const int32_t* ids, const float* dis, int K,
+                          int32_t* G, void* ws, int* d_err, cudaStream_t st) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int64_t n = dv.n;
+  const size_t big_cap = pow2_size((size_t)n + R);
+  uint8_t* w = (uint8_t*)ws;
+  auto take = [&](size_t bytes) {
+    uint8_t* r = w;
+    w += al(bytes);
+    return r;
+  };
+  int32_t* iota = (int32_t*)take((size_t)n * 4);
+  int32_t* vis_cnt = (int32_t*)take((size_t)n * 4);
+  int32_t* cnt = (int32_t*)take((size_t)n * 4);
+  int32_t* fillc = (int32_t*)take((size_t)n * 4);
+  int32_t* off = (int32_t*)take((size_t)n * 4);
+  int32_t* targets = (int32_t*)take((size_t)n * R * 4);
+  int32_t* src = (int32_t*)take((size_t)n * R * 4);
+  int32_t* big = (int32_t*)take((size_t)n * R * 4);
+  int32_t* counters = (int32_t*)take(64);
+  uint64_t* big_keys = (uint64_t*)take((size_t)BIG_WARPS * big_cap * 8);
+  int32_t* big_alive = (int32_t*)take((size_t)BIG_WARPS * big_cap * 8);
+  cudaError_t e;
+  set_where("graph prune: clear");
+  if ((e = cudaMemsetAsync(G, 0xff, (size_t)n * R * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(cnt, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(fillc, 0, (size_t)n * 4, st)) != cudaSuccess) return e;
+  k_iota_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8), 256, 0, st>>>(n, iota, vis_cnt,
+                                                                                                      K);
+  note_launch();
+  BuildArgs b;
+  memset(&b, 0, sizeof(b));
+  b.X = dv.X;
+  b.row_bytes = dv.row_bytes;
+  b.n = n;
+  b.C = dv.C;
+  b.G = G;
+  b.R = R;
+  b.a2 = alpha * alpha;
+  b.batch = iota;
+  b.m = n;
+  b.vis_ids = ids;
+  b.vis_dis = dis;
+  b.vis_cnt = vis_cnt;
+  b.vcap = K;
+  b.cap_new = (int)pow2_size((size_t)K + R);
+  b.cnt = cnt;
+  b.fillc = fillc;
+  b.off = off;
+  b.targets = targets;
+  b.ntargets = counters;
+  b.cursor = counters + 1;
+  b.nbig = counters + 2;
+  b.src = src;
+  b.big = big;
+  b.big_keys = big_keys;
+  b.big_alive = big_alive;
+  b.big_cap = (int)big_cap;
+  b.err = d_err;
+  return prune_reverse_batch(dv, b, n, counters, st);
+}
+
 cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t* d_order, int32_t* G,
                       int32_t* d_degree, void* ws, int* d_err, int log2h, cudaStream_t st) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -505,10 +639,6 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
   a.vis_cnt = vis_cnt;
   a.err = d_err;
 
-  const size_t new_smem_warp = (size_t)cap_new * 12 + (size_t)R * 8;
-  const int new_wpb = new_smem_warp * 4 <= 200 * 1024 ? 4 : (new_smem_warp * 2 <= 200 * 1024 ? 2 : 1);
-  const size_t rev_smem_warp = (size_t)PRUNE_CAP * 16 + (size_t)R * 4;
-  const int rev_wpb = 2;
   const int sms = num_sms();
   const int passes = p.build_passes == 2 ? 2 : 1;
 
@@ -524,41 +654,7 @@ cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t*
     if ((e = launch_search(dv, a, st)) != cudaSuccess) return e;
     b.batch = d_order + pos;
     b.m = m;
-    e = dispatch_layout(dv, [&](auto dt, auto met, auto wv, auto cpl) -> cudaError_t {
-      constexpr int DT = decltype(dt)::value, MET = decltype(met)::value;
-      constexpr int W = decltype(wv)::value, CPL = decltype(cpl)::value;
-      auto kn = k_prune_new<DT, MET, W, CPL>;
-      size_t sm = new_smem_warp * new_wpb;
-      set_where("build: prune attribute");
-      cudaError_t ee = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (ee != cudaSuccess) return ee;
-      set_where("build: prune launch");
-      int64_t blocks = std::min<int64_t>((m + new_wpb - 1) / new_wpb, (int64_t)sms * 8);
-      kn<<<(unsigned)blocks, new_wpb * 32, sm, st>>>(b); note_launch();
-      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
-      set_where("build: reverse-edge counters");
-      if ((ee = cudaMemsetAsync(counters, 0, 64, st)) != cudaSuccess) return ee;
-      int64_t edges = m * R;
-      unsigned eb = (unsigned)std::min<int64_t>((edges + 255) / 256, (int64_t)sms * 16);
-      set_where("build: reverse-edge count");
-      k_rev_count<<<eb, 256, 0, st>>>(b); note_launch();
-      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
-      set_where("build: reverse-edge offsets");
-      k_rev_offsets<<<eb, 256, 0, st>>>(b); note_launch();
-      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
-      set_where("build: reverse-edge fill");
-      k_rev_fill<<<eb, 256, 0, st>>>(b); note_launch();
-      if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
-      auto ka = k_rev_apply<DT, MET, W, CPL>;
-      size_t sm2 = rev_smem_warp * rev_wpb;
-      set_where("build: reverse-edge apply");
-      if ((ee = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
-        return ee;
-      unsigned ab = (unsigned)std::min<int64_t>((edges + rev_wpb - 1) / rev_wpb, (int64_t)sms * 8);
-      ka<<<ab, rev_wpb * 32, sm2, st>>>(b); note_launch();
-      k_rev_apply_big<DT, MET, W, CPL><<<BIG_WARPS, 32, 0, st>>>(b); note_launch();
-      return cudaGetLastError();
-    });
+    e = prune_reverse_batch(dv, b, m, counters, st);
     if (e != cudaSuccess) return e;
     pos += m;
     bsz = std::min(2 * bsz, cap);  // doubling stops at the cap (no overflow)

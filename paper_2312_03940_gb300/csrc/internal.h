@@ -179,6 +179,15 @@ pecann_status run_density_bf(const DataView& fv, const pecann_params* p, int32_t
 pecann_status run_dep_bf(const DataView& fv, const float* rank_key, const int32_t* U, int64_t nu, int32_t* lam,
                          float* delta, int* err, void* bws, int64_t* h_counts, cudaStream_t st);
 
+// NN-Descent graph index (nnd.cu). fv: FP32 or uint8 rows; init: device
+// repeats x n x K ids; h_changes (host, repeats x rounds) and knn_out (device
+// n x K) may be NULL; ws: nndescent_ws_bytes(n, K, repeats, R) bytes.
+size_t nndescent_ws_bytes(int64_t n, int K, int repeats, int R);
+cudaError_t run_nndescent(const DataView& fv, int K, int repeats, const int32_t* init, int rounds, float alpha, int R,
+                          int32_t* G, int32_t* knn_out, int64_t* h_changes, void* ws, int* d_err, cudaStream_t st);
+// Out-degrees of an n x R graph (build.cu).
+__global__ void k_degree(int64_t n, int R, const int32_t* G, int32_t* deg);
+
 int num_sms();
 // Counts the kernels the library launches (reported by pecann_kernel_launches).
 void note_launch();

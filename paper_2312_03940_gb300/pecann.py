@@ -53,8 +53,8 @@ class PecannClusterSetting(ctypes.Structure):
 
 EXPORTS = ["pecann_params_default", "pecann_status_string", "pecann_last_error", "pecann_version",
            "pecann_kernel_launches",
-           "pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
-           "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
+           "pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_nndescent_workspace_size",
+           "pecann_build_nndescent", "pecann_density", "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
            "pecann_batch_prepare", "pecann_run_batched", "pecann_cluster_workspace_size", "pecann_cluster_sweep"]
 
 NOALLOC_MAX_POINTS = 1 << 20
@@ -92,6 +92,8 @@ def load_library(path: str | None = None):
     lib.pecann_workspace_size.argtypes = [D, P, ctypes.POINTER(sz)]
     lib.pecann_search.argtypes = [D, vp, i32, vp, i64, vp, i32, i32, i32, vp, vp, vp, P, vp, sz, vp]
     lib.pecann_build_graph.argtypes = [D, P, vp, vp, vp, vp, sz, vp]
+    lib.pecann_nndescent_workspace_size.argtypes = [D, P, i32, i32, ctypes.POINTER(sz)]
+    lib.pecann_build_nndescent.argtypes = [D, P, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]
     lib.pecann_density.argtypes = [D, vp, P, vp, vp, vp, vp, vp, sz, vp]
     lib.pecann_dependent_points.argtypes = [D, vp, P, vp, vp, vp, vp, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.pecann_cluster.argtypes = [i64, vp, vp, vp, P, vp, ctypes.POINTER(i64), vp, sz, vp]
@@ -99,7 +101,8 @@ def load_library(path: str | None = None):
     lib.pecann_cluster_workspace_size.argtypes = [i64, i32, ctypes.POINTER(sz)]
     lib.pecann_cluster_sweep.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, ctypes.POINTER(PecannClusterSetting),
                                          vp, ctypes.POINTER(i64), vp, sz, vp]
-    for f in ["pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_density",
+    for f in ["pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_nndescent_workspace_size",
+              "pecann_build_nndescent", "pecann_density",
               "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
               "pecann_batch_prepare", "pecann_run_batched", "pecann_cluster_workspace_size", "pecann_cluster_sweep"]:
         getattr(lib, f).restype = ctypes.c_int
@@ -226,6 +229,31 @@ def pecann_build_graph(ds: Dataset, p: PecannParams, order: torch.Tensor | None 
     _check(load_library().pecann_build_graph(ds.ref, ctypes.byref(p), _ptr(order), _ptr(graph), _ptr(degree),
                                              _ptr(ws), ws.numel(), _stream(stream)))
     return graph, degree
+
+
+def pecann_build_nndescent(ds: Dataset, p: PecannParams, K: int, init: torch.Tensor, rounds: int,
+                           ws: torch.Tensor | None = None, stream=None):
+    """NN-Descent graph index from the initial lists init (repeats, n, K) int32
+    on the device. Returns dict graph (n,R), degree (n,), knn (n,K) int32 and
+    changes (repeats, rounds) int64 on the host."""
+    _cuda(init, "init", torch.int32)
+    if init.dim() != 3 or init.shape[1] != ds.n or init.shape[2] != K:
+        raise ValueError("init must have shape (repeats, n, K)")
+    repeats = init.shape[0]
+    lib = load_library()
+    if ws is None:
+        nb = ctypes.c_size_t(0)
+        _check(lib.pecann_nndescent_workspace_size(ds.ref, ctypes.byref(p), K, repeats, ctypes.byref(nb)))
+        ws = torch.empty(nb.value, dtype=torch.uint8, device=ds.X.device)
+    dev = ds.X.device
+    graph = torch.empty((ds.n, p.R), dtype=torch.int32, device=dev)
+    degree = torch.empty(ds.n, dtype=torch.int32, device=dev)
+    knn = torch.empty((ds.n, K), dtype=torch.int32, device=dev)
+    changes = torch.zeros((repeats, max(rounds, 1)), dtype=torch.int64)  # host
+    _check(lib.pecann_build_nndescent(ds.ref, ctypes.byref(p), K, repeats, _ptr(init), rounds, _ptr(graph),
+                                      _ptr(degree), _ptr(knn), ctypes.c_void_p(changes.data_ptr()),
+                                      _ptr(ws), ws.numel(), _stream(stream)))
+    return dict(graph=graph, degree=degree, knn=knn, changes=changes[:, :rounds].numpy())
 
 
 def pecann_density(ds: Dataset, graph: torch.Tensor, p: PecannParams, ws: torch.Tensor | None = None,

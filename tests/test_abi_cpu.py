@@ -132,3 +132,24 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "workspace ok" in r.stdout and "bad center function" in r.stdout
+
+
+def test_nndescent_checks_on_host(lib):
+    """NN-Descent workspace sizing, argument checks and a short workspace
+    answer on the host (fake device pointers, never dereferenced)."""
+    p = pc.params(R=24, alpha=1.2)
+    ds = pc.PecannDataset(256, 100_000, 128, pc.U8, pc.L2, 0, None, None)
+    b = ctypes.c_size_t(0)
+    assert lib.pecann_nndescent_workspace_size(ctypes.byref(ds), ctypes.byref(p), 16, 2, ctypes.byref(b)) == pc.OK
+    # at least the two list buffers, the reverse keys and both repeats' lists
+    assert b.value >= 100_000 * 16 * (4 * 4 + 8 + 2 * 4 * 2)
+    for K, reps in ((0, 1), (65, 1), (16, 0), (16, 65)):
+        assert lib.pecann_nndescent_workspace_size(ctypes.byref(ds), ctypes.byref(p), K, reps,
+                                                   ctypes.byref(b)) == pc.EINVAL
+    g = ctypes.c_void_p(256)
+    call = lib.pecann_build_nndescent
+    assert call(ctypes.byref(ds), ctypes.byref(p), 16, 1, None, 5, g, None, None, None, g, 1 << 40, None) == pc.EINVAL
+    assert call(ctypes.byref(ds), ctypes.byref(p), 16, 1, g, -1, g, None, None, None, g, 1 << 40, None) == pc.EINVAL
+    bad = pc.params(R=24, alpha=0.9)
+    assert call(ctypes.byref(ds), ctypes.byref(bad), 16, 1, g, 5, g, None, None, None, g, 1 << 40, None) == pc.EINVAL
+    assert call(ctypes.byref(ds), ctypes.byref(p), 16, 1, g, 5, g, None, None, None, g, 64, None) == pc.ENOMEM
