@@ -154,10 +154,21 @@ def replica_throughput(points_per_rank: int, steps: int, world: int, elapsed_s: 
     return world * points_per_rank * steps / elapsed_s
 
 
-def source_sha() -> str:
+# the sources each profiled kernel is built from: a profile's counters stand
+# for the kernel only while these files are unchanged
+KERNEL_SOURCES = {
+    "k_bf_screen": ["bf_screen.cu", "tcgen05.cuh", "common.cuh", "internal.h"],
+    "k_search": ["search.cu", "search_kernel.cuh", "search_common.cuh", "search_u8.cu", "search_f32.cu",
+                 "search_f32ip.cu", "search_bf16.cu", "search_fp8.cu", "dispatch.cuh", "common.cuh", "internal.h"],
+}
+
+
+def source_sha(kernel: str | None = None) -> str:
+    """Digest of the named kernel's sources (all of csrc/ when None)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2312_03940_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    files = KERNEL_SOURCES.get(kernel) if kernel else None
+    for f in sorted(files if files else os.listdir(csrc)):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -175,7 +186,7 @@ def profiled_traffic(kernel_tag: str):
             if ":" in line:
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("source_sha") != source_sha():
+    if vals.get("source_sha") != source_sha(vals.get("kernel_sources")):
         return None
     try:
         return float(vals["traffic_bytes_per_launch_full"])

@@ -37,8 +37,9 @@
 //                chunk is first reduced to its smallest key and only chunks
 //                that beat the heap's largest key are taken apart. At the end
 //                of a query tile the two sorted halves are merged.
-// All CTAs sweep the point tiles in the same order, so a point tile read from
-// HBM serves every CTA from L2.
+// All CTAs sweep the point tiles in the same order and are kept within a few
+// epochs of one another (pace_enter), so a point tile read from HBM serves
+// every CTA from L2.
 #include <string.h>
 
 #include <algorithm>
@@ -92,6 +93,13 @@ struct ScreenArgs {
   const float* in_thr;    // per query row
   int cap;
   int* err;
+  // pacing (NULL: none): CTA producers count their arrivals at every epoch
+  // of pace_every point tiles in pace[epoch]; before entering epoch e a
+  // producer waits (bounded) until every CTA of the grid that sweeps epoch
+  // e - pace_lag has entered it
+  int* pace;
+  int pace_every, pace_lag;
+  int64_t pace_epochs;    // entries of pace[]
 };
 
 __device__ __forceinline__ bool rank_above_key(float kj, int32_t j, float ki, int32_t i) {
@@ -182,6 +190,37 @@ __device__ __forceinline__ void heap_sort(float* hk, int32_t* hi, int et, int cn
   }
 }
 
+constexpr uint64_t SC_PACE_NS = 100000000ull;  // 100 ms: then the CTA stops pacing
+
+// Pacing of the point-tile sweep. Every CTA reads the whole point set once
+// per query tile; the point rows (n x d BF16) are far larger than L2, so a
+// tile read from HBM serves the other CTAs only while they sweep close to
+// one another. Without a bound the CTAs drift apart over thousands of
+// tiles and most tiles come from HBM again for each CTA. So the producer
+// announces every epoch of pace_every tiles it enters and does not enter
+// epoch e before all CTAs that sweep epoch e - pace_lag have entered that
+// one. The grid is co-resident (cooperative launch) and the wait is bounded:
+// after SC_PACE_NS the CTA gives up pacing for the rest of the launch, which
+// changes its speed only, never its results. Returns whether to go on pacing.
+__device__ __forceinline__ bool pace_enter(const ScreenArgs& a, int64_t epoch, int64_t epr, int64_t groups, int CL) {
+  if (epoch >= a.pace_epochs) return false;
+  atomicAdd(a.pace + epoch, 1);
+  const int64_t e2 = epoch - a.pace_lag;
+  if (e2 < 0) return true;
+  // CTAs that sweep epoch e2: those with a query tile in its round
+  const int64_t n_cl = gridDim.x / CL, round = e2 / epr;
+  const int64_t left = groups - round * n_cl;
+  const int need = (int)(CL * (left < n_cl ? left : n_cl));
+  const volatile int* c = a.pace + e2;
+  if (*c >= need) return true;
+  const uint64_t t0 = tc::globaltimer_ns();
+  for (;;) {
+    __nanosleep(256);
+    if (*c >= need) return true;
+    if (tc::globaltimer_ns() - t0 > SC_PACE_NS) return false;
+  }
+}
+
 // CL: CTAs per cluster. With CL > 1 the CTAs of a cluster take CL
 // consecutive query tiles and sweep the point tiles in lockstep: each loads
 // 1/CL of every point chunk (tb's box is SC_N / CL rows) and multicasts it to
@@ -244,9 +283,15 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
       tc::prefetch_tmap(&tb);
       uint64_t it = 0;  // chunk loads issued
       bool ok = true;
-      for (int64_t g = cl_id; g * CL < n_qt && ok; g += n_cl) {
+      bool pacing = a.pace != nullptr;
+      const int64_t epr = (n_pt + a.pace_every - 1) / (a.pace_every > 0 ? a.pace_every : 1);
+      const int64_t groups = (n_qt + CL - 1) / CL;
+      int64_t round = 0;
+      for (int64_t g = cl_id; g * CL < n_qt && ok; g += n_cl, round++) {
         const int64_t qt = g * CL + crank;
         for (int64_t pt = 0; pt < n_pt && ok; pt++) {
+          if (pacing && pt % a.pace_every == 0)
+            pacing = pace_enter(a, round * epr + pt / a.pace_every, epr, groups, CL);
           for (int c = 0; c < a.kc; c++) {
             const int s = (int)(it % SC_STAGES);
             const uint32_t ph = (uint32_t)((it / SC_STAGES) & 1);
@@ -442,25 +487,32 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
         // merge the two sorted halves of the row (up to SC_KEEP entries)
         const int p2 = et + 128;
         const int n0 = cnt, n1 = half_cnt[p2];
-        int i0 = 0, i1 = 0, m = 0;
+        // the exact decision needs only the entries up to the reference and
+        // those within the band above it (mb of them): a point whose
+        // approximate key exceeds ref_key + 2E has a canonical key above
+        // ref_key + E, the most the reference's canonical key can be
+        int i0 = 0, i1 = 0, m = 0, mb = 0;
         const int ref = MODE == SCR_KNN ? a.k - 1 : 0;
-        float ref_key = INFINITY;
+        float ref_key = INFINITY, lim = INFINITY;
         int32_t* out = a.out_ids + r * SC_KEEP;
         while (i0 < n0 || i1 < n1) {
           const bool take0 = i1 >= n1 || (i0 < n0 && hk[i0 * SC_EPI + et] <= hk[i1 * SC_EPI + p2]);
           const float kk = take0 ? hk[i0 * SC_EPI + et] : hk[i1 * SC_EPI + p2];
           const int32_t id = take0 ? hi[i0 * SC_EPI + et] : hi[i1 * SC_EPI + p2];
           if (take0) i0++; else i1++;
-          if (m == ref) ref_key = kk;
+          if (m == ref) {
+            ref_key = kk;
+            lim = ref_key + 2.0f * E;
+          }
+          if (m <= ref || kk <= lim) mb = m + 1;
           out[m++] = id;
         }
         // complete when each half either kept every point it saw, or its
         // largest kept key lies beyond the band around the reference key
-        const float lim = ref_key + 2.0f * E;
         const bool c0ok = n0 < SC_HALF || hk[(n0 - 1) * SC_EPI + et] > lim;
         const bool c1ok = n1 < SC_HALF || hk[(n1 - 1) * SC_EPI + p2] > lim;
         if (m <= ref || (c0ok && c1ok)) {
-          a.out_cnt[r] = m;
+          a.out_cnt[r] = mb;
         } else {
           a.out_cnt[r] = -1;
           a.out_thr[r] = lim;
@@ -596,9 +648,12 @@ static size_t screen_smem() {
   return 1024 + (size_t)SC_STAGES * SC_STAGE_BYTES + 2 * (size_t)SC_HALF * SC_EPI * 4;
 }
 
+constexpr int64_t SC_PACE_MAX = 65536;  // entries of the pacing counters
+
 template <int MODE, int PASS, int METRIC, int CL>
-static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int64_t n, int d, const ScreenArgs& a,
+static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int64_t n, int d, const ScreenArgs& a_in,
                                    cudaStream_t st) {
+  ScreenArgs a = a_in;
   auto kern = k_bf_screen<MODE, PASS, METRIC, CL>;
   const size_t smem = screen_smem();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -622,6 +677,7 @@ static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = CL > 1 ? 1 : 0;
+  const int64_t n_pt = (n + SC_N - 1) / SC_N;
   // a persistent grid: as many clusters as can be resident at once (a
   // cluster's CTAs share one GPC, so with CL > 1 that can be fewer than
   // SMs / CL), never more than there are groups of query tiles
@@ -633,7 +689,41 @@ static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int
     cudaGetLastError();
   }
   cfg.gridDim = dim3((unsigned)(CL * std::max<int64_t>(1, std::min<int64_t>(groups, resident))));
+  // pacing (see pace_enter): single-CTA clusters, point rows larger than
+  // about a third of L2, a grid that is co-resident (cooperative launch);
+  // the lead is bounded to about 32 MB of point rows in 4 epochs
+  bool pace = false;
+  if (CL == 1 && a.pace && (int64_t)n * d * 2 > ((int64_t)48 << 20) && cfg.gridDim.x > 1) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SC_THREADS, smem) == cudaSuccess && occ >= 1 &&
+        (int64_t)cfg.gridDim.x <= (int64_t)occ * num_sms()) {
+      const int64_t tile_bytes = (int64_t)SC_N * d * 2;
+      int64_t every = std::max<int64_t>(1, std::max<int64_t>(4, ((int64_t)32 << 20) / tile_bytes) / 4);
+      const int64_t rounds = (groups + cfg.gridDim.x - 1) / cfg.gridDim.x;
+      while (rounds * ((n_pt + every - 1) / every) > SC_PACE_MAX) every *= 2;
+      if (every <= (int64_t)1 << 30) {
+        a.pace_every = (int)every;
+        a.pace_lag = 4;
+        a.pace_epochs = rounds * ((n_pt + every - 1) / every);
+        pace = cudaMemsetAsync(a.pace, 0, (size_t)a.pace_epochs * 4, st) == cudaSuccess;
+      }
+    }
+    cudaGetLastError();
+  }
+  if (!pace) a.pace = nullptr;
+  if (pace) {
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.numAttrs = 1;
+  }
   e = cudaLaunchKernelEx(&cfg, kern, ta, tb, a);
+  if (e != cudaSuccess && pace) {
+    // the cooperative form was refused: the same launch without pacing
+    cudaGetLastError();
+    a.pace = nullptr;
+    cfg.numAttrs = 0;
+    e = cudaLaunchKernelEx(&cfg, kern, ta, tb, a);
+  }
   note_launch();
   if (e != cudaSuccess) set_where("brute-force screen: launch");
   return e;
@@ -686,11 +776,12 @@ struct BfWs {
   int32_t* fb;           // n query ids for the exact SIMT kernels
   int32_t* counters;     // [0] overflowed rows, [1] SIMT rows
   float* rkpad;          // dependent passes: rank keys, padded past n with NaN
+  int* pace;             // SC_PACE_MAX pacing counters of the screen
 };
 
 size_t bf_ws_bytes(int64_t n, int d) {
-  return 2 * al256((size_t)n * d * 2) + al256((size_t)n * SC_KEEP * 4) + 9 * al256((size_t)n * 4) +
-         al256((size_t)SC_N * 4) + 512 + al256((size_t)(n + SC_N) * 4);
+  return 2 * al256((size_t)n * d * 2) + al256((size_t)n * SC_KEEP * 4) + 8 * al256((size_t)n * 4) +
+         al256((size_t)SC_N * 4) + 256 + 256 + SC_PACE_MAX * 4 + al256((size_t)(n + SC_N) * 4);
 }
 
 static BfWs carve_bf(void* ws, int64_t n, int d) {
@@ -712,8 +803,9 @@ static BfWs carve_bf(void* ws, int64_t n, int d) {
   w.ovf_ids = (int32_t*)take((size_t)n * 4);
   w.ovf_thr = (float*)take((size_t)n * 4);
   w.fb = (int32_t*)take((size_t)n * 4);
-  w.maxbits = (unsigned*)take((size_t)n * 4);
+  w.maxbits = (unsigned*)take(256);
   w.counters = (int32_t*)take(256);
+  w.pace = (int*)take((size_t)SC_PACE_MAX * 4);
   w.rkpad = (float*)take((size_t)(n + SC_N) * 4);
   return w;
 }
@@ -765,6 +857,7 @@ static ScreenArgs base_args(const DataView& fv, const BfWs& w, int* err) {
   a.maxnorm = reinterpret_cast<const float*>(w.maxbits);
   eps_of(fv, &a);
   a.err = err;
+  a.pace = w.pace;
   return a;
 }
 
