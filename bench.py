@@ -52,6 +52,9 @@ U8 = dict(n=1_000_000, d=128, components=100, R=64, L=128, alpha=1.2, k=10, n_cl
           n_start=8192, build_passes=2)
 U8_NAME = ("u8-gaussian-mixture n=1,000,000 d=128 (100 components, Zipf 1.1 weights, sigma U[5,20], "
            "5% uniform noise); kth density k=10; product center 100")
+# NN-Descent graph of the uint8 rows (report line): K-lists, 3 repeats and alpha 1.1 as in the paper's
+# comparison of graph indices; rounds stop earlier when no list changes
+NND = dict(K=32, repeats=3, rounds=12, alpha=1.1)
 CPU_SAMPLE = 16       # points per oracle timing sample (brute-force index on the full rows)
 CPU_SAMPLE_GRAPH = 256  # points per oracle timing sample (beam search on the same graph)
 RECALL_QUERIES = 200  # FP64 exact k-NN of sampled points (CPU)
@@ -604,6 +607,31 @@ def u8_variants(args, dev, stream, threads):
                              "sample": (f"oracle beam search (Algorithm 1) k-NN + kth density of "
                                         f"{CPU_SAMPLE_GRAPH * 4} sampled points on the same graph")}}
     del path
+    # NN-Descent graph on the same rows, searched with the same beam
+    init = torch.from_numpy(synth.random_neighbours(n, NND["K"], repeats=NND["repeats"])).to(dev)
+    pn = pc.params(R=U8["R"], alpha=NND["alpha"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nnd = pc.pecann_build_nndescent(ds, pn, NND["K"], init, NND["rounds"])
+    torch.cuda.synchronize()
+    nnd_build_s = time.perf_counter() - t0
+    del init
+    path = Path(ds, nnd["graph"], p, dev)
+    el_n, dms_n = timed(path.step, 2, steps, stream)
+    nnd_dist = path.dens["knn_dist"].cpu().numpy()
+    nnd_labels = path.labels.cpu().numpy()
+    nnd_line = {"metric": METRIC, "value": n / (el_n / steps), "unit": UNIT, "dtype": "u8",
+                "ms_per_step": el_n * 1000 / steps, "steps": steps, "warmup": 2,
+                "config": {"workload": name,
+                           "index": (f"NN-Descent graph K={NND['K']}, {NND['repeats']} repeats, <= {NND['rounds']} "
+                                     f"rounds, RobustPrune alpha {NND['alpha']} to R={U8['R']}; beam {U8['L']}")},
+                "density_ms": dms_n, "build_s": nnd_build_s,
+                "nndescent_changes_per_round": nnd["changes"].tolist(),
+                "dep_rounds": int(path.stats[0]), "unfinished_after_round0": int(path.stats[1]),
+                "brute_force_tail": int(path.stats[63]),
+                "recall": exact_recall(X, 0, nnd_dist, U8["k"], m=2000), "recall_queries": 2000}
+    del path, nnd
+    torch.cuda.empty_cache()
     # exact index on the same rows
     pb = pc.params(k=U8["k"], R=U8["R"], L_search=U8["L"], L_dep=U8["L"], center=pc.CENTER_PRODUCT,
                    n_clusters=U8["n_clusters"], index=pc.INDEX_BRUTE_FORCE)
@@ -614,6 +642,9 @@ def u8_variants(args, dev, stream, threads):
     line["recall_full_n_vs_exact_index"] = full_recall(graph_dist, ex_dist)
     line["ari_vs_exact_index"] = exact.ari(graph_labels, path.labels.cpu().numpy())
     out.append(line)
+    nnd_line["recall_full_n_vs_exact_index"] = full_recall(nnd_dist, ex_dist)
+    nnd_line["ari_vs_exact_index"] = exact.ari(nnd_labels, path.labels.cpu().numpy())
+    out.append(nnd_line)
     rate_cpu_bf, _ = cpu_knn_rate(X, 0, None, 0, U8["k"], CPU_SAMPLE * 4, threads)
     out.append({"metric": METRIC, "value": n / (el / args.variant_steps), "unit": UNIT, "dtype": "u8",
                 "ms_per_step": el * 1000 / args.variant_steps, "steps": args.variant_steps, "warmup": 1,

@@ -337,8 +337,7 @@ __global__ void __launch_bounds__(128) k_b_bf_knn(SearchArgs a, const BatchTable
       }
       __syncwarp();
       if (nc) {
-        eval_cands<DT_F32, METRIC, 32, CPL>(la, w, nc, qv, lane);
-        merge_cands(w, nb, a.k, nc, cursor, lane);
+        eval_merge<DT_F32, METRIC, 32, CPL>(la, w, nc, qv, lane, nb, a.k, cursor);
       }
     }
     const int c = min(nb, a.k);

@@ -117,12 +117,12 @@ __global__ void __launch_bounds__(128) k_nnd_init(NndArgs r) {
       w.cids[t] = (uint32_t)y < (uint32_t)a.n ? y : (int32_t)u;
     }
     __syncwarp();
-    eval_cands<DT, METRIC, W, CPL>(a, w, r.K, qv, lane);
-    for (int t = lane; t < r.K; t += 32)
-      if (w.cids[t] == (int32_t)u) w.ckeys[t] = KEY_NONE;
+    const int m = eval_cands<DT, METRIC, W, CPL>(a, w, r.K, qv, lane);  // every key kept (m == K)
+    for (int t = lane; t < m; t += 32)
+      if (key_id(w.ckeys[t]) == (int32_t)u) w.ckeys[t] = KEY_NONE;
     __syncwarp();
     int nb = 0, cursor = 0;
-    merge_cands(w, nb, r.K, r.K, cursor, lane);
+    merge_cands(w, nb, r.K, m, cursor, lane);
     if (nb < r.K && lane == 0) set_error(a.err, ERR_BAD_ID);  // repeated or invalid initial ids
     write_list(w, nb, r.K, r.N2, r.N2d, u, lane);
     __syncwarp();
@@ -163,16 +163,14 @@ __global__ void __launch_bounds__(128) k_nnd_round(NndArgs r) {
       const int32_t p = s < K ? __ldg(r.N + u * K + s) : __ldg(r.Rv + u * K + (s - K));
       if (p < 0) continue;
       if (nc + 2 * K > a.stage) {
-        eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-        merge_cands(w, nb, K, nc, cursor, lane);
+        eval_merge<DT, METRIC, W, CPL>(a, w, nc, qv, lane, nb, K, cursor);
         nc = 0;
       }
       nc = admit_row(a, w, r.N + (int64_t)p * K, K, (int32_t)u, nc, lane, lt, &bad);
       nc = admit_row(a, w, r.Rv + (int64_t)p * K, K, (int32_t)u, nc, lane, lt, &bad);
     }
     if (nc) {
-      eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-      merge_cands(w, nb, K, nc, cursor, lane);
+      eval_merge<DT, METRIC, W, CPL>(a, w, nc, qv, lane, nb, K, cursor);
     }
     if (__any_sync(FULL, bad) && lane == 0) set_error(a.err, ERR_BAD_ID);
     write_list(w, nb, K, r.N2, r.N2d, u, lane);

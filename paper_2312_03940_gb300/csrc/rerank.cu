@@ -43,8 +43,7 @@ __global__ void __launch_bounds__(128) k_rerank_knn(RerankArgs r) {
       const int nc = min(a.stage, c - c0);
       for (int i = lane; i < nc; i += 32) w.cids[i] = r.cand[u * r.K + c0 + i];
       __syncwarp();
-      eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-      merge_cands(w, nb, a.k, nc, cursor, lane);
+      eval_merge<DT, METRIC, W, CPL>(a, w, nc, qv, lane, nb, a.k, cursor);
     }
     for (int t = lane; t < a.k; t += 32) {
       const uint64_t e = key_clean(w.beam[t]);
@@ -78,8 +77,8 @@ __global__ void __launch_bounds__(128) k_rerank_dep(RerankArgs r) {
       const int nc = min(a.stage, c - c0);
       for (int i = lane; i < nc; i += 32) w.cids[i] = r.cand[u * r.K + c0 + i];
       __syncwarp();
-      eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-      for (int i = lane; i < nc; i += 32) best = w.ckeys[i] < best ? w.ckeys[i] : best;
+      const int m = eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);  // every key kept
+      for (int i = lane; i < m; i += 32) best = w.ckeys[i] < best ? w.ckeys[i] : best;
       __syncwarp();
     }
 #pragma unroll

@@ -148,8 +148,7 @@ __global__ void __launch_bounds__(128) k_bf_knn(BfKnnArgs b) {
       }
       __syncwarp();
       if (nc) {
-        eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-        merge_cands(w, nb, a.k, nc, cursor, lane);
+        eval_merge<DT, METRIC, W, CPL>(a, w, nc, qv, lane, nb, a.k, cursor);
       }
     }
     const int cnt = min(nb, a.k);

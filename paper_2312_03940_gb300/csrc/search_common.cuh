@@ -126,11 +126,26 @@ __device__ __forceinline__ int gather_start(const SearchArgs& a, WarpSmem& w, in
   return nc;
 }
 
-// Keys (canonical distance to the query, id) of the staged candidates.
+// Append the keys of this pass that beat `worst` (those a full beam could
+// take) to the front of ckeys: `has` marks the lanes that hold a key.
+__device__ __forceinline__ void keep_keys(WarpSmem& w, bool has, uint64_t key, uint64_t worst, int& m,
+                                          unsigned lt) {
+  const bool keep = has && key < worst;
+  const unsigned mk = __ballot_sync(FULL, keep);
+  if (keep) w.ckeys[m + __popc(mk & lt)] = key;
+  m += __popc(mk);
+}
+
+// Keys (canonical distance to the query, id) of the staged candidates; the
+// ones below `worst` are packed at the front of ckeys (in no particular
+// order) and their number is returned. With worst = KEY_NONE every key is
+// kept.
 template <int DT, int METRIC, int W, int CPL, int QC>
-__device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int nc,
-                                           const uint4 (&qv)[QC], int lane) {
+__device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int nc, const uint4 (&qv)[QC],
+                                          int lane, uint64_t worst = KEY_NONE) {
   constexpr int GR = 32 / W;
+  const unsigned lt = lanemask_lt();
+  int m = 0;
   constexpr int UNR = CPL >= 4 ? 1 : (CPL == 1 ? 4 : 2);
   const int g = lane / W, gl = lane % W;
   if (nc > GR * UNR) {
@@ -151,7 +166,8 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
         unsigned k = Partial<DT_U8, MET_L2, CPL>::run(qv, r1);
         k += __shfl_xor_sync(FULL, k, 2);
         k += __shfl_xor_sync(FULL, k, 1);
-        if (gl == 0 && c < nc) w.ckeys[c] = make_key_nonneg((float)k, w.cids[c]);
+        const bool has = gl == 0 && c < nc;
+        keep_keys(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, worst, m, lt);
         break;
       }
     }
@@ -189,8 +205,9 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
           s.y = 1.0f - s.y;
         }
         const int c = c0 + u * GR + g, c1 = c + GR;
-        if (gl == 0 && c < nc) w.ckeys[c] = make_key(s.x, w.cids[c]);
-        if (gl == 0 && c1 < nc) w.ckeys[c1] = make_key(s.y, w.cids[c1]);
+        const bool h0 = gl == 0 && c < nc, h1 = gl == 0 && c1 < nc;
+        keep_keys(w, h0, h0 ? make_key(s.x, w.cids[c]) : KEY_NONE, worst, m, lt);
+        keep_keys(w, h1, h1 ? make_key(s.y, w.cids[c1]) : KEY_NONE, worst, m, lt);
       }
     } else if constexpr (DT == DT_U8 && UNR == 2) {
       // the same for two rows per lane group: one split step, then plain
@@ -203,7 +220,8 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
 #pragma unroll
       for (int off = W / 4; off >= 1; off >>= 1) k += __shfl_xor_sync(FULL, k, off);
       const int c = c0 + (int)b * GR + g;
-      if ((gl & (W / 2 - 1)) == 0 && c < nc) w.ckeys[c] = make_key_nonneg((float)k, w.cids[c]);
+      const bool has = (gl & (W / 2 - 1)) == 0 && c < nc;
+      keep_keys(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, worst, m, lt);
     } else if constexpr (DT == DT_U8 && UNR == 4) {
       // integer partials, exact in any order: reduce the group's four rows
       // together. The first two steps halve the rows a lane carries (it keeps
@@ -221,18 +239,22 @@ __device__ __forceinline__ void eval_cands(const SearchArgs& a, WarpSmem& w, int
 #pragma unroll
       for (int off = W / 8; off >= 1; off >>= 1) k += __shfl_xor_sync(FULL, k, off);
       const int c = c0 + (2 * (int)b2 + (int)b1) * GR + g;
-      if ((gl & (W / 4 - 1)) == 0 && c < nc) w.ckeys[c] = make_key_nonneg((float)k, w.cids[c]);
+      const bool has = (gl & (W / 4 - 1)) == 0 && c < nc;
+      keep_keys(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, worst, m, lt);
     } else {
 #pragma unroll
       for (int u = 0; u < UNR; u++) {
         float dv = group_dis<DT, METRIC, W, CPL>(qv, r[u]);
         int c = c0 + u * GR + g;
-        if (gl == 0 && c < nc)
-          w.ckeys[c] = METRIC == MET_L2 ? make_key_nonneg(dv, w.cids[c]) : make_key(dv, w.cids[c]);
+        const bool has = gl == 0 && c < nc;
+        uint64_t key = KEY_NONE;
+        if (has) key = METRIC == MET_L2 ? make_key_nonneg(dv, w.cids[c]) : make_key(dv, w.cids[c]);
+        keep_keys(w, has, key, worst, m, lt);
       }
     }
   }
   __syncwarp();
+  return m;
 }
 
 // Number of entries of the sorted clean keys s[0..m) below x.
@@ -393,6 +415,16 @@ __device__ __forceinline__ int merge_cands(WarpSmem& w, int& nb, int Lw, int nc,
     m += __popc(bm);
     __syncwarp();
   }
+  return merge_filtered(w, nb, Lw, m, cursor, lane);
+}
+
+// Score the nc staged candidates and merge those a full beam could take.
+// Returns the number of keys merged. Collective.
+template <int DT, int METRIC, int W, int CPL, int QC>
+__device__ __forceinline__ int eval_merge(const SearchArgs& a, WarpSmem& w, int nc, const uint4 (&qv)[QC],
+                                          int lane, int& nb, int Lw, int& cursor) {
+  const uint64_t worst = nb >= Lw ? key_clean(w.beam[Lw - 1]) : KEY_NONE;
+  const int m = eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane, worst);
   return merge_filtered(w, nb, Lw, m, cursor, lane);
 }
 

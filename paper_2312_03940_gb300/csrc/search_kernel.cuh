@@ -80,8 +80,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
   for (int s0 = 0; a.S && s0 < a.nS; s0 += a.stage) {
     nc = gather_start(a, w, q, s0, lane, lt, &bad, &q_in_s);
     if (nc) {
-      eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-      merge_cands(w, nb, a.Lw, nc, cursor, lane);
+      eval_merge<DT, METRIC, W, CPL>(a, w, nc, qv, lane, nb, a.Lw, cursor);
       evals += nc;
     }
   }
@@ -90,8 +89,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
     nc = gather_out(a, w, q, q, lane, lt, &bad);
     iters = 1;
     if (nc) {
-      eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-      merge_cands(w, nb, a.Lw, nc, cursor, lane);
+      eval_merge<DT, METRIC, W, CPL>(a, w, nc, qv, lane, nb, a.Lw, cursor);
       evals += nc;
     }
   }
@@ -113,8 +111,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, WarpSmem& w, int
     // L <- L u E_out(p*), keeping the Lw closest
     nc = gather_out(a, w, p, q, lane, lt, &bad);
     if (nc) {
-      eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
-      merge_cands(w, nb, a.Lw, nc, cursor, lane);
+      eval_merge<DT, METRIC, W, CPL>(a, w, nc, qv, lane, nb, a.Lw, cursor);
       evals += nc;
     }
     if (++iters > a.n + 1) {
