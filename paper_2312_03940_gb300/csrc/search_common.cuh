@@ -146,7 +146,10 @@ __device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int 
   constexpr int GR = 32 / W;
   const unsigned lt = lanemask_lt();
   int m = 0;
-  constexpr int UNR = CPL >= 4 ? 1 : (CPL == 1 ? 4 : 2);
+  // rows per lane group per pass (the 4-lane uint8 layout takes 4: one L2
+  // round trip covers 32 rows)
+  constexpr bool U8W4 = DT == DT_U8 && W == 4 && CPL == 2;
+  constexpr int UNR = CPL >= 4 ? 1 : (CPL == 1 || U8W4 ? 4 : 2);
   const int g = lane / W, gl = lane % W;
   if (nc > GR * UNR) {
     // rows beyond the first batch: start their fetch now, so the later
