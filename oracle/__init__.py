@@ -71,6 +71,13 @@ def _load():
         _lib.orc_knn_density_rows.restype = ctypes.c_int
         _lib.orc_nndescent.argtypes = [P, i32, i32, vp, i32, f32, i32, vp, vp, vp, ctypes.c_int]
         _lib.orc_nndescent.restype = ctypes.c_int
+        u64 = ctypes.c_uint64
+        _lib.orc_hcnng.argtypes = [P, i32, i32, i32, f32, i32, u64, vp, vp, ctypes.c_int]
+        _lib.orc_hcnng.restype = ctypes.c_int
+        _lib.orc_hcnng_partition.argtypes = [P, i32, i32, u64, vp, vp]
+        _lib.orc_hcnng_partition.restype = i64
+        _lib.orc_hcnng_leaf_mst.argtypes = [P, vp, i64, i32, vp]
+        _lib.orc_hcnng_leaf_mst.restype = i64
         _lib.orc_dependent_points.argtypes = [P, vp, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp,
                                               ctypes.c_int]
         _lib.orc_dependent_points.restype = ctypes.c_int
@@ -207,6 +214,39 @@ def nndescent(P: Points, K: int, init: np.ndarray, rounds: int, alpha: float, R:
     if rc:
         raise ValueError("orc_nndescent: bad arguments")
     return dict(knn=knn, G=G, changes=ch[:, :rounds])
+
+
+def hcnng(P: Points, repeats: int, leaf_size: int, mst_deg: int, alpha: float, R: int, seed: int = 0,
+          threads: int | None = None):
+    """HCNNG graph index (the paper's HCNNG option, Sec. 5.1): per repeat a
+    random hierarchical split into leaves of at most leaf_size points and a
+    degree-bounded minimum spanning forest in every leaf; the union of the
+    forests, pruned by RobustPrune. Returns dict G (n,R) int32, leaves
+    (repeats,) int64."""
+    G = np.empty((P.n, R), np.int32)
+    leaves = np.zeros(repeats, np.int64)
+    rc = _load().orc_hcnng(P.ptr, repeats, leaf_size, mst_deg, alpha, R, seed, _p(G), _p(leaves),
+                           threads or default_threads())
+    if rc:
+        raise ValueError("orc_hcnng: bad arguments")
+    return dict(G=G, leaves=leaves)
+
+
+def hcnng_partition(P: Points, t: int, leaf_size: int, seed: int = 0):
+    """The leaves of HCNNG tree t: list of int32 id arrays, in order."""
+    order = np.empty(P.n, np.int32)
+    begin = np.empty(P.n + 1, np.int64)
+    nl = _load().orc_hcnng_partition(P.ptr, t, leaf_size, seed, _p(order), _p(begin))
+    return [order[begin[i]:begin[i + 1]].copy() for i in range(nl)]
+
+
+def hcnng_leaf_mst(P: Points, ids: np.ndarray, mst_deg: int):
+    """Degree-bounded minimum spanning forest of the points ids (ascending):
+    (e, 2) int32 id pairs in the order they were taken."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    edges = np.empty((max(len(ids) - 1, 1), 2), np.int32)
+    ne = _load().orc_hcnng_leaf_mst(P.ptr, _p(ids), len(ids), mst_deg, _p(edges))
+    return edges[:ne]
 
 
 def dependent_points(P: Points, G: np.ndarray, key: np.ndarray, knn_ids: np.ndarray, Ld: int,

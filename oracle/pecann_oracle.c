@@ -24,6 +24,9 @@
  *                         paper names it without steps: synchronous rounds of
  *                         Dong et al.'s method, see its own comment)
  *   orc_knn_density_rows  Algorithm 2 lines 2-4 for a list of points only
+ *   orc_hcnng             HCNNG graph index (Sec. 5.1, graph indices; named
+ *                         without steps: random hierarchical splits and
+ *                         degree-bounded spanning forests, see its comment)
  *
  * Where the paper leaves a point open, this file takes the readings below:
  *  - Canonical FP32 dissimilarity. For rows a, b of d elements (d % 4 == 0) 32
@@ -1262,5 +1265,229 @@ int orc_nndescent(const orc_points* P, int32_t K, int32_t repeats, const int32_t
   free(N2);
   free(Nd);
   free(N);
+  return 0;
+}
+
+/* ---------- HCNNG graph index (Sec. 5.1, graph indices) ---------- */
+
+/*
+ * The paper's framework also offers HCNNG graphs (Munoz et al., "Hierarchical
+ * clustering-based graphs for large scale approximate nearest neighbor
+ * search"), repeated num_repeats times and pruned with alpha, but prints no
+ * steps. This follows the method's outline in a deterministic form:
+ *   for each repeat t: split the points hierarchically -- a node [b, b + m)
+ *     of the current order with more than leaf_size points draws two pivots
+ *     p1 != p2 from its points; every point with dis(x, p1) <= dis(x, p2)
+ *     goes left, the rest right, each side keeping its order (a split that
+ *     leaves a side empty cuts the node at ceil(m / 2) instead);
+ *     in every leaf, a minimum spanning forest whose degrees are bounded by
+ *     mst_deg: the leaf's pairs in (dis, smaller id, larger id) order, each
+ *     taken when it joins two components and both ends have degree below
+ *     mst_deg (Kruskal's rule with the bound);
+ *   C(u) = the neighbours of u in the forests of all repeats;
+ *   G(u) = RobustPrune(u, C(u), alpha, R).
+ * The order starts as 0..n-1, so every node lists its points in ascending id.
+ * Pivot draws use SplitMix64 (Steele, Lea and Flood 2014) as a counter-based
+ * generator keyed by (seed, t, b, m, j): v = S(seed + t), v = S(v + b),
+ * v = S(v + m), draw j = S(v + j), where S(x) is SplitMix64's output for the
+ * state x; p1 = the (draw 0 mod m)-th point of the node, p2 = the
+ * (draw 1 mod (m - 1))-th of the others.
+ */
+static uint64_t sm64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static uint64_t hc_draw(uint64_t seed, int32_t t, int64_t b, int64_t m, int j) {
+  uint64_t v = sm64(seed + (uint64_t)t);
+  v = sm64(v + (uint64_t)b);
+  v = sm64(v + (uint64_t)m);
+  return sm64(v + (uint64_t)j);
+}
+
+/* The leaves of tree t: order (n ids) and leaf_begin (n_leaves + 1 offsets,
+   in the order the leaves lie in `order`). Returns the number of leaves. */
+int64_t orc_hcnng_partition(const orc_points* P, int32_t t, int32_t leaf_size, uint64_t seed, int32_t* order,
+                            int64_t* leaf_begin) {
+  const int64_t n = P->n;
+  for (int64_t i = 0; i < n; i++) order[i] = (int32_t)i;
+  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  uint8_t* is_leaf_start = (uint8_t*)calloc((size_t)n + 1, 1);
+  int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * 2 * ((size_t)n + 1));
+  int64_t sp = 0;
+  stack[sp++] = 0;
+  stack[sp++] = n;
+  while (sp > 0) {
+    const int64_t m = stack[--sp], b = stack[--sp];
+    if (m <= leaf_size) {
+      is_leaf_start[b] = 1;
+      continue;
+    }
+    const int64_t i1 = (int64_t)(hc_draw(seed, t, b, m, 0) % (uint64_t)m);
+    int64_t i2 = (int64_t)(hc_draw(seed, t, b, m, 1) % (uint64_t)(m - 1));
+    if (i2 >= i1) i2++;
+    const int32_t p1 = order[b + i1], p2 = order[b + i2];
+    int64_t nl = 0, nr = 0;
+    for (int64_t i = 0; i < m; i++) {
+      const int32_t x = order[b + i];
+      if (orc_dis(P, x, p1) <= orc_dis(P, x, p2))
+        order[b + nl++] = x; /* in place: nl <= i, the left side never overtakes */
+      else
+        tmp[nr++] = x;
+    }
+    for (int64_t i = 0; i < nr; i++) order[b + nl + i] = tmp[i];
+    if (nl == 0 || nl == m) nl = (m + 1) / 2; /* degenerate split: halves of the same order */
+    stack[sp++] = b;
+    stack[sp++] = nl;
+    stack[sp++] = b + nl;
+    stack[sp++] = m - nl;
+  }
+  int64_t nleaf = 0;
+  for (int64_t i = 0; i < n; i++)
+    if (is_leaf_start[i]) leaf_begin[nleaf++] = i;
+  leaf_begin[nleaf] = n;
+  free(stack);
+  free(is_leaf_start);
+  free(tmp);
+  return nleaf;
+}
+
+typedef struct {
+  float dis;
+  int32_t i, j; /* local indices, i < j */
+} hc_edge;
+
+static int hc_edge_cmp(const void* pa, const void* pb) {
+  const hc_edge* a = (const hc_edge*)pa;
+  const hc_edge* b = (const hc_edge*)pb;
+  if (a->dis != b->dis) return a->dis < b->dis ? -1 : 1;
+  if (a->i != b->i) return a->i < b->i ? -1 : 1;
+  return a->j < b->j ? -1 : (a->j > b->j);
+}
+
+static int32_t hc_find(int32_t* parent, int32_t x) {
+  while (parent[x] != x) {
+    parent[x] = parent[parent[x]];
+    x = parent[x];
+  }
+  return x;
+}
+
+/* Degree-bounded minimum spanning forest of the m points ids (ascending).
+   Writes its edges as id pairs (at most m - 1) and returns their number. */
+int64_t orc_hcnng_leaf_mst(const orc_points* P, const int32_t* ids, int64_t m, int32_t mst_deg, int32_t* edges) {
+  if (m < 2) return 0;
+  const int64_t ne = m * (m - 1) / 2;
+  hc_edge* E = (hc_edge*)malloc(sizeof(hc_edge) * (size_t)ne);
+  int64_t e = 0;
+  for (int32_t i = 0; i < m; i++)
+    for (int32_t j = i + 1; j < m; j++) {
+      E[e].dis = orc_dis(P, ids[i], ids[j]);
+      E[e].i = i;
+      E[e].j = j;
+      e++;
+    }
+  qsort(E, (size_t)ne, sizeof(hc_edge), hc_edge_cmp);
+  int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+  int32_t* deg = (int32_t*)calloc((size_t)m, sizeof(int32_t));
+  for (int32_t i = 0; i < m; i++) parent[i] = i;
+  int64_t out = 0;
+  for (int64_t k = 0; k < ne && out < m - 1; k++) {
+    const int32_t i = E[k].i, j = E[k].j;
+    if (deg[i] >= mst_deg || deg[j] >= mst_deg) continue;
+    const int32_t ri = hc_find(parent, i), rj = hc_find(parent, j);
+    if (ri == rj) continue;
+    parent[ri < rj ? rj : ri] = ri < rj ? ri : rj;
+    deg[i]++;
+    deg[j]++;
+    edges[2 * out] = ids[i];
+    edges[2 * out + 1] = ids[j];
+    out++;
+  }
+  free(deg);
+  free(parent);
+  free(E);
+  return out;
+}
+
+typedef struct {
+  const orc_points* P;
+  const int32_t* order;
+  const int64_t* leaf_begin;
+  int32_t mst_deg;
+  int32_t* edges;      /* 2 (n - 1) per tree at most: leaf l writes from 2 * leaf_begin[l] */
+  int64_t* leaf_ne;
+} hc_leaf_ctx;
+
+static void hc_leaf_body(void* c, int64_t l, int tid) {
+  (void)tid;
+  const hc_leaf_ctx* x = (const hc_leaf_ctx*)c;
+  const int64_t b = x->leaf_begin[l], m = x->leaf_begin[l + 1] - b;
+  x->leaf_ne[l] = orc_hcnng_leaf_mst(x->P, x->order + b, m, x->mst_deg, x->edges + 2 * b);
+}
+
+typedef struct {
+  const orc_points* P;
+  const int32_t* cand; /* n x cap neighbour ids */
+  const int32_t* ncand;
+  int32_t cap;
+  float alpha;
+  int32_t R;
+  int32_t* G;
+} hc_prune_ctx;
+
+static void hc_prune_body(void* c, int64_t u, int tid) {
+  (void)tid;
+  const hc_prune_ctx* x = (const hc_prune_ctx*)c;
+  const int32_t nc = x->ncand[u];
+  item* C = (item*)malloc(sizeof(item) * (size_t)(nc > 0 ? nc : 1));
+  int32_t* out = (int32_t*)malloc(sizeof(int32_t) * (size_t)x->R);
+  for (int32_t t = 0; t < nc; t++) {
+    C[t].id = x->cand[u * x->cap + t];
+    C[t].dis = orc_dis(x->P, u, C[t].id);
+  }
+  const int32_t deg = robust_prune(x->P, u, C, nc, x->alpha, x->R, out);
+  for (int32_t t = 0; t < x->R; t++) x->G[u * x->R + t] = t < deg ? out[t] : -1;
+  free(out);
+  free(C);
+}
+
+/* HCNNG graph (see above): G n x R, -1 padded. leaves (may be NULL): the
+   number of leaves of each repeat. Returns 0, or 1 on bad arguments. */
+int orc_hcnng(const orc_points* P, int32_t repeats, int32_t leaf_size, int32_t mst_deg, float alpha, int32_t R,
+              uint64_t seed, int32_t* G, int64_t* leaves, int nthreads) {
+  const int64_t n = P->n;
+  if (repeats < 1 || leaf_size < 2 || mst_deg < 1 || R < 1 || n < 2) return 1;
+  const int32_t cap = repeats * mst_deg;
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int64_t* leaf_begin = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+  int64_t* leaf_ne = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+  int32_t* edges = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)n);
+  int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * (size_t)n * (size_t)cap);
+  int32_t* ncand = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  for (int32_t t = 0; t < repeats; t++) {
+    const int64_t nl = orc_hcnng_partition(P, t, leaf_size, seed, order, leaf_begin);
+    if (leaves) leaves[t] = nl;
+    hc_leaf_ctx lc = {P, order, leaf_begin, mst_deg, edges, leaf_ne};
+    parallel_for(nl, nthreads, hc_leaf_body, &lc);
+    for (int64_t l = 0; l < nl; l++) {
+      const int32_t* E = edges + 2 * leaf_begin[l];
+      for (int64_t e = 0; e < leaf_ne[l]; e++) {
+        const int32_t a = E[2 * e], b = E[2 * e + 1];
+        cand[(int64_t)a * cap + ncand[a]++] = b; /* a tree gives each point at most mst_deg edges */
+        cand[(int64_t)b * cap + ncand[b]++] = a;
+      }
+    }
+  }
+  hc_prune_ctx pc = {P, cand, ncand, cap, alpha, R, G};
+  parallel_for(n, nthreads, hc_prune_body, &pc);
+  free(ncand);
+  free(cand);
+  free(edges);
+  free(leaf_ne);
+  free(leaf_begin);
+  free(order);
   return 0;
 }

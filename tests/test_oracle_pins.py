@@ -678,3 +678,105 @@ def test_nndescent_graph_invariants_and_recall():
     for u in range(3000):
         row = G[u][: deg[u]]
         assert (G[u][deg[u]:] == -1).all() and u not in row and len(set(row.tolist())) == len(row)
+
+
+# ---------------------------------------------------------------- HCNNG (Sec. 5.1, graph indices)
+
+def _scipy_mst_edges(X):
+    """The minimum spanning tree of all points under the oracle's ordering
+    value, as a set of (smaller id, larger id) (scipy's routine)."""
+    sparse = pytest.importorskip("scipy.sparse.csgraph")
+    P = oracle.Points(X)
+    n = len(X)
+    W = np.zeros((n, n))
+    for i in range(n):
+        for j in range(i + 1, n):
+            W[i, j] = oracle.dis(P, i, j)
+    assert (W[np.triu_indices(n, 1)] > 0).all()  # scipy reads 0 as "no edge"
+    T = sparse.minimum_spanning_tree(W).tocoo()
+    return {(min(a, b), max(a, b)) for a, b in zip(T.row.tolist(), T.col.tolist())}, W
+
+
+def test_hcnng_leaf_forest_without_bound_is_the_mst():
+    """With a degree bound no point can reach, the leaf forest is the minimum
+    spanning tree (distinct distances: it is unique), as scipy computes it."""
+    X = np.random.default_rng(41).normal(size=(60, 8)).astype(np.float32)
+    mst, W = _scipy_mst_edges(X)
+    E = oracle.hcnng_leaf_mst(oracle.Points(X), np.arange(60), mst_deg=60)
+    assert len(E) == 59
+    assert {(min(a, b), max(a, b)) for a, b in E.tolist()} == mst
+    # the edges come out in increasing length (Kruskal's order)
+    w = [W[min(a, b), max(a, b)] for a, b in E.tolist()]
+    assert w == sorted(w)
+
+
+def test_hcnng_leaf_forest_degree_bound():
+    """Points on a line: the MST is the path through them in coordinate
+    order, whose degrees are at most 2, so the bound 2 leaves it unchanged;
+    the bound 1 leaves a matching of disjoint closest pairs."""
+    g = np.random.default_rng(42)
+    t = np.sort(g.uniform(0, 100, size=40)).astype(np.float32)
+    perm = g.permutation(40)
+    X = np.zeros((40, 4), np.float32)
+    X[perm, 0] = t  # point perm[i] sits at the i-th coordinate
+    P = oracle.Points(X)
+    E = oracle.hcnng_leaf_mst(P, np.arange(40), mst_deg=2)
+    path = {(min(perm[i], perm[i + 1]), max(perm[i], perm[i + 1])) for i in range(39)}
+    assert {(min(a, b), max(a, b)) for a, b in E.tolist()} == path
+    M = oracle.hcnng_leaf_mst(P, np.arange(40), mst_deg=1)
+    deg = np.bincount(M.ravel(), minlength=40)
+    assert deg.max() == 1
+    # greedy matching: the globally closest pair of the line is in it
+    gaps = np.diff(t)
+    i = int(np.argmin(gaps))
+    assert (min(perm[i], perm[i + 1]), max(perm[i], perm[i + 1])) in {(min(a, b), max(a, b)) for a, b in M.tolist()}
+
+
+def test_hcnng_partition_invariants():
+    X, _ = _mixture(2000, 16, 6, np.random.default_rng(43))
+    P = oracle.Points(X)
+    for t in range(3):
+        L = oracle.hcnng_partition(P, t, leaf_size=150, seed=7)
+        allids = np.concatenate(L)
+        assert sorted(allids.tolist()) == list(range(2000))       # a partition of the points
+        assert max(len(l) for l in L) <= 150 and len(L) >= 14      # leaves of at most leaf_size
+        assert all((np.diff(l) > 0).all() for l in L)              # each leaf in ascending id
+    # the draws depend on the repeat and the seed, and on nothing else
+    a = oracle.hcnng_partition(P, 0, 150, seed=7)
+    b = oracle.hcnng_partition(P, 0, 150, seed=7)
+    c = oracle.hcnng_partition(P, 1, 150, seed=7)
+    d = oracle.hcnng_partition(P, 0, 150, seed=8)
+    assert all((x == y).all() for x, y in zip(a, b))
+    assert len(a) != len(c) or any(not np.array_equal(x, y) for x, y in zip(a, c))
+    assert len(a) != len(d) or any(not np.array_equal(x, y) for x, y in zip(a, d))
+    # one leaf when it can hold every point
+    one = oracle.hcnng_partition(P, 0, 2000)
+    assert len(one) == 1 and (one[0] == np.arange(2000)).all()
+
+
+def test_hcnng_graph_is_the_mst_when_nothing_is_cut_or_pruned():
+    """One repeat, one leaf, no degree bound and alpha so large that
+    RobustPrune drops nothing: every point's list is its MST neighbours."""
+    X = np.random.default_rng(44).normal(size=(50, 8)).astype(np.float32)
+    mst, _ = _scipy_mst_edges(X)
+    G = oracle.hcnng(oracle.Points(X), repeats=1, leaf_size=50, mst_deg=50, alpha=1e6, R=50)["G"]
+    got = {(min(u, v), max(u, v)) for u in range(50) for v in G[u].tolist() if v >= 0}
+    assert got == mst
+    for u in range(50):  # both directions of every edge
+        row = [v for v in G[u].tolist() if v >= 0]
+        assert sorted(row) == sorted([b if a == u else a for a, b in mst if u in (a, b)])
+
+
+def test_hcnng_graph_invariants_and_recall():
+    X, _ = _mixture(3000, 32, 8, np.random.default_rng(45))
+    P = oracle.Points(X)
+    r = oracle.hcnng(P, repeats=3, leaf_size=200, mst_deg=3, alpha=1.2, R=24)
+    G = r["G"]
+    deg = (G >= 0).sum(1)
+    assert deg.max() <= 9 and deg.min() >= 1  # at most mst_deg per repeat
+    for u in range(3000):
+        row = G[u][: deg[u]]
+        assert (G[u][deg[u]:] == -1).all() and u not in row and len(set(row.tolist())) == len(row)
+    _, ed = exact.exact_knn(X, 10)
+    o = oracle.knn_density(P, G, L=64, k=10)
+    assert exact.knn_recall(o["dist"], ed) >= 0.95
