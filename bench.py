@@ -55,6 +55,9 @@ U8_NAME = ("u8-gaussian-mixture n=1,000,000 d=128 (100 components, Zipf 1.1 weig
 # NN-Descent graph of the uint8 rows (report line): K-lists, 3 repeats and alpha 1.1 as in the paper's
 # comparison of graph indices; rounds stop earlier when no list changes
 NND = dict(K=32, repeats=3, rounds=12, alpha=1.1)
+# HCNNG graph of the uint8 rows (report line): 3 repeats as in the same comparison, leaves of up to
+# 200 points (the kernel's limit), spanning forests of degree <= 3
+HC = dict(repeats=3, leaf=200, mst_deg=3, alpha=1.1)
 CPU_SAMPLE = 16       # points per oracle timing sample (brute-force index on the full rows)
 CPU_SAMPLE_GRAPH = 256  # points per oracle timing sample (beam search on the same graph)
 RECALL_QUERIES = 200  # FP64 exact k-NN of sampled points (CPU)
@@ -70,6 +73,9 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="headline only: no variants, recall, e2e or CPU baseline")
     ap.add_argument("--variant-steps", type=int, default=2, help="timed steps of each report line")
+    ap.add_argument("--graph-line-only", action="store_true",
+                    help="u8-1m / vmf1024-graph: the Vamana FP32 (or uint8) graph line alone, without CPU baseline, "
+                         "e2e or recall (for short profiling runs)")
     ap.add_argument("--workload", default="vmf1024",
                     choices=["vmf1024", "vmf1024-graph", "u8-1m", "batched64", "sphere384"],
                     help="vmf1024: the benchmark line (with its variants); vmf1024-graph / u8-1m: report lines alone")
@@ -537,6 +543,11 @@ def vmf_graph_variants(args, X, Xd, exact_dist, exact_labels, dev, stream, threa
              ("fp8-e4m3", pc.Dataset(Xf8, metric=pc.IP, dim_scale=scale, data_f32=Xd), 1)]
     out = []
     base_name = VMF_NAME if n == VMF["n"] else VMF_NAME.replace("1,280,000", f"{n:,}")
+    if args.graph_line_only:
+        path = Path(ds32, G, p, dev)
+        el, dms = timed(path.step, 1, args.variant_steps, stream)
+        return [{"metric": METRIC, "value": n / (el / args.variant_steps), "unit": UNIT, "dtype": "fp32",
+                 "ms_per_step": el * 1000 / args.variant_steps, "density_ms": dms, "build_s": build_s}]
     rate_cpu, _ = cpu_knn_rate(X, 1, Gh, VMF["L"], VMF["k"], CPU_SAMPLE_GRAPH, threads)
     for tag, ds, s in kinds:
         path = Path(ds, G, p, dev)
@@ -592,6 +603,9 @@ def u8_variants(args, dev, stream, threads):
     el, dms = timed(path.step, 2, steps, stream)
     graph_dist = path.dens["knn_dist"].cpu().numpy()
     graph_labels = path.labels.cpu().numpy()
+    if args.graph_line_only:
+        return [{"metric": METRIC, "value": n / (el / steps), "unit": UNIT, "dtype": "u8",
+                 "ms_per_step": el * 1000 / steps, "density_ms": dms, "build_s": build_s}]
     rate_cpu, _ = cpu_knn_rate(X, 0, Gh, U8["L"], U8["k"], CPU_SAMPLE_GRAPH * 4, threads)
     line = {"metric": METRIC, "value": n / (el / steps), "unit": UNIT, "dtype": "u8",
             "ms_per_step": el * 1000 / steps, "steps": steps, "warmup": 2,
@@ -632,6 +646,30 @@ def u8_variants(args, dev, stream, threads):
                 "recall": exact_recall(X, 0, nnd_dist, U8["k"], m=2000), "recall_queries": 2000}
     del path, nnd
     torch.cuda.empty_cache()
+    # HCNNG graph on the same rows, searched with the same beam
+    ph = pc.params(R=U8["R"], alpha=HC["alpha"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hc = pc.pecann_build_hcnng(ds, ph, HC["repeats"], HC["leaf"], HC["mst_deg"])
+    torch.cuda.synchronize()
+    hc_build_s = time.perf_counter() - t0
+    path = Path(ds, hc["graph"], p, dev)
+    el_h, dms_h = timed(path.step, 2, steps, stream)
+    hc_dist = path.dens["knn_dist"].cpu().numpy()
+    hc_labels = path.labels.cpu().numpy()
+    hc_line = {"metric": METRIC, "value": n / (el_h / steps), "unit": UNIT, "dtype": "u8",
+               "ms_per_step": el_h * 1000 / steps, "steps": steps, "warmup": 2,
+               "config": {"workload": name,
+                          "index": (f"HCNNG graph, {HC['repeats']} repeats, leaves <= {HC['leaf']}, forest degree "
+                                    f"<= {HC['mst_deg']}, RobustPrune alpha {HC['alpha']} to R={U8['R']}; "
+                                    f"beam {U8['L']}")},
+               "density_ms": dms_h, "build_s": hc_build_s, "hcnng_leaves": hc["leaves"].tolist(),
+               "mean_degree": float(hc["degree"].float().mean().item()),
+               "dep_rounds": int(path.stats[0]), "unfinished_after_round0": int(path.stats[1]),
+               "brute_force_tail": int(path.stats[63]),
+               "recall": exact_recall(X, 0, hc_dist, U8["k"], m=2000), "recall_queries": 2000}
+    del path, hc
+    torch.cuda.empty_cache()
     # exact index on the same rows
     pb = pc.params(k=U8["k"], R=U8["R"], L_search=U8["L"], L_dep=U8["L"], center=pc.CENTER_PRODUCT,
                    n_clusters=U8["n_clusters"], index=pc.INDEX_BRUTE_FORCE)
@@ -645,6 +683,9 @@ def u8_variants(args, dev, stream, threads):
     nnd_line["recall_full_n_vs_exact_index"] = full_recall(nnd_dist, ex_dist)
     nnd_line["ari_vs_exact_index"] = exact.ari(nnd_labels, path.labels.cpu().numpy())
     out.append(nnd_line)
+    hc_line["recall_full_n_vs_exact_index"] = full_recall(hc_dist, ex_dist)
+    hc_line["ari_vs_exact_index"] = exact.ari(hc_labels, path.labels.cpu().numpy())
+    out.append(hc_line)
     rate_cpu_bf, _ = cpu_knn_rate(X, 0, None, 0, U8["k"], CPU_SAMPLE * 4, threads)
     out.append({"metric": METRIC, "value": n / (el / args.variant_steps), "unit": UNIT, "dtype": "u8",
                 "ms_per_step": el * 1000 / args.variant_steps, "steps": args.variant_steps, "warmup": 1,
@@ -676,11 +717,13 @@ def run_vmf_graph_only(args):
     Xd = torch.from_numpy(X).to(dev)
     p = pc.params(k=VMF["k"], L_search=VMF["L"], center=pc.CENTER_PRODUCT, n_clusters=VMF["n_clusters"],
                   index=pc.INDEX_BRUTE_FORCE)
-    ref = Path(pc.Dataset(Xd, metric=pc.IP), None, p, dev)
-    ref.step(None)
-    ex_dist, ex_labels = ref.dens["knn_dist"].cpu().numpy(), ref.labels.cpu().numpy()
-    del ref
-    torch.cuda.empty_cache()
+    ex_dist = ex_labels = None
+    if not args.graph_line_only:
+        ref = Path(pc.Dataset(Xd, metric=pc.IP), None, p, dev)
+        ref.step(None)
+        ex_dist, ex_labels = ref.dens["knn_dist"].cpu().numpy(), ref.labels.cpu().numpy()
+        del ref
+        torch.cuda.empty_cache()
     out = vmf_graph_variants(args, X, Xd, ex_dist, ex_labels, dev, torch.cuda.current_stream(),
                              oracle.default_threads())
     print(json.dumps({"workload": "vmf1024-graph", "lines": out}), flush=True)

@@ -18,10 +18,10 @@
  *    do not matter; on return they are undefined.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
  *    queued on it. pecann_search, pecann_build_graph, pecann_build_nndescent,
- *    pecann_density, pecann_density_noalloc and pecann_dependent_points
- *    return only after their work on `stream` has finished (they read back
- *    an error word or small counters); the other calls are asynchronous
- *    unless a host output is requested.
+ *    pecann_build_hcnng, pecann_density, pecann_density_noalloc and
+ *    pecann_dependent_points return only after their work on `stream` has
+ *    finished (they read back an error word or small counters); the other
+ *    calls are asynchronous unless a host output is requested.
  *  - Errors are returned as pecann_status; nothing is thrown across the ABI.
  *    PECANN_EINVAL: an argument is out of range (checked on the host before
  *    any GPU work); PECANN_ENOMEM: ws_bytes is too small; PECANN_ECUDA: a
@@ -262,6 +262,39 @@ PECANN_API pecann_status pecann_build_nndescent(const pecann_dataset* ds, const 
                                                 int32_t repeats, const int32_t* d_init, int32_t rounds,
                                                 int32_t* d_graph, int32_t* d_degree, int32_t* d_knn,
                                                 int64_t* h_changes, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * HCNNG graph index (Sec. 5.1, graph indices: the framework also takes HCNNG
+ * graphs, repeated num_repeats times and pruned with alpha; the paper prints
+ * no steps). The library follows the outline of Munoz et al.'s HCNNG in a
+ * deterministic form:
+ *   for each repeat t: split the points hierarchically. A node [b, b + m) of
+ *     the current order (initially 0..n-1) with more than leaf_size points
+ *     draws two pivots p1 != p2 among its points: p1 is its (d0 mod m)-th
+ *     point, p2 the (d1 mod (m - 1))-th of the others, where d_j =
+ *     S(S(S(S(seed + t) + b) + m) + j) and S(x) is the SplitMix64 output for
+ *     the state x (Steele, Lea and Flood 2014). Points with
+ *     dis(x, p1) <= dis(x, p2) go left, the rest right, each side keeping its
+ *     order; a split that leaves a side empty cuts the node at ceil(m / 2).
+ *     In every leaf, a minimum spanning forest with degrees at most mst_deg:
+ *     the leaf's pairs in (dis, smaller id, larger id) order, each taken when
+ *     it joins two components and both ends have degree below mst_deg;
+ *   C(u) = u's neighbours in the forests of all repeats;
+ *   G(u) = RobustPrune(u, C(u), alpha, R) (no reverse-edge step).
+ * 1 <= repeats <= 64, 2 <= leaf_size <= 200 (a leaf's pair keys are sorted
+ * in shared memory), 1 <= mst_deg <= 16; reads p->R, p->alpha and p->seed.
+ * FP32 (or uint8) rows: BF16 / FP8 datasets use data_f32.
+ * Outputs: d_graph (n x R, -1 padded); d_degree (n, may be NULL); h_leaves
+ * (HOST, repeats int64, may be NULL): the number of leaves of each repeat.
+ * Blocks until done.
+ */
+PECANN_API pecann_status pecann_hcnng_workspace_size(const pecann_dataset* ds, const pecann_params* p,
+                                                     int32_t repeats, int32_t leaf_size, int32_t mst_deg,
+                                                     size_t* bytes);
+PECANN_API pecann_status pecann_build_hcnng(const pecann_dataset* ds, const pecann_params* p, int32_t repeats,
+                                            int32_t leaf_size, int32_t mst_deg, int32_t* d_graph,
+                                            int32_t* d_degree, int64_t* h_leaves, void* ws, size_t ws_bytes,
+                                            void* stream);
 
 /*
  * k nearest neighbours and density of every point (Algorithm 2 lines 2-4).

@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpecann.so")
 SOURCES = ["search.cu", "search_u8.cu", "search_f32.cu", "search_f32ip.cu", "search_bf16.cu", "search_fp8.cu",
            "search_batched.cu", "rerank.cu", "dep.cu", "cluster.cu", "build.cu", "abi.cu", "noalloc.cu", "batched.cu",
-           "bf_screen.cu", "nnd.cu"]
+           "bf_screen.cu", "nnd.cu", "hcnng.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(HERE, "..", "include")]

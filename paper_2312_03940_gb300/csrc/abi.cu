@@ -518,6 +518,55 @@ pecann_status pecann_build_nndescent(const pecann_dataset* ds, const pecann_para
   return read_err(&h->err, st);
 }
 
+static pecann_status check_hcnng(const DataView& dv, const pecann_params* p, int32_t repeats, int32_t leaf_size,
+                                 int32_t mst_deg) {
+  if (repeats < 1 || repeats > 64) return set_last_error("repeats must be in 1..64"), PECANN_EINVAL;
+  if (leaf_size < 2 || leaf_size > HCNNG_MAX_LEAF)
+    return set_last_error("leaf_size must be in 2..200"), PECANN_EINVAL;
+  if (mst_deg < 1 || mst_deg > HCNNG_MAX_DEG) return set_last_error("mst_deg must be in 1..16"), PECANN_EINVAL;
+  if (p->R < 1 || p->R > 256) return set_last_error("R must be in 1..256"), PECANN_EINVAL;
+  if (!(p->alpha >= 1.0f)) return set_last_error("alpha must be >= 1"), PECANN_EINVAL;
+  (void)dv;
+  return PECANN_OK;
+}
+
+pecann_status pecann_hcnng_workspace_size(const pecann_dataset* ds, const pecann_params* p, int32_t repeats,
+                                          int32_t leaf_size, int32_t mst_deg, size_t* bytes) {
+  DataView dv0, dv;
+  pecann_status s = check_dataset(ds, &dv0, &dv);
+  if (s) return s;
+  if (!p || !bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
+  if ((s = check_hcnng(dv, p, repeats, leaf_size, mst_deg))) return s;
+  *bytes = HDR + hcnng_ws_bytes(dv.n, repeats, leaf_size, mst_deg);
+  return PECANN_OK;
+}
+
+pecann_status pecann_build_hcnng(const pecann_dataset* ds, const pecann_params* p, int32_t repeats,
+                                 int32_t leaf_size, int32_t mst_deg, int32_t* d_graph, int32_t* d_degree,
+                                 int64_t* h_leaves, void* ws, size_t ws_bytes, void* stream) {
+  DataView dv0, dv;
+  pecann_status s = check_dataset(ds, &dv0, &dv);  // FP32 (or U8) rows, like the other builds
+  if (s) return s;
+  if (!p || !d_graph || !ws) return set_last_error("NULL pointer"), PECANN_EINVAL;
+  if ((s = check_hcnng(dv, p, repeats, leaf_size, mst_deg))) return s;
+  if (ws_bytes < HDR + hcnng_ws_bytes(dv.n, repeats, leaf_size, mst_deg))
+    return set_last_error("workspace too small"), PECANN_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* h = (WsHeader*)ws;
+  cudaError_t e = cudaMemsetAsync(h, 0, HDR, st);
+  if (e != cudaSuccess) return cuda_status(e, "memset");
+  e = run_hcnng(dv, repeats, leaf_size, mst_deg, p->alpha, p->R, p->seed, d_graph, h_leaves, (uint8_t*)ws + HDR,
+                &h->err, st);
+  if ((s = cuda_status(e, "hcnng"))) return s;
+  if (d_degree) {
+    k_degree<<<(unsigned)std::min<int64_t>((dv.n + 255) / 256, (int64_t)num_sms() * 8), 256, 0, st>>>(
+        dv.n, p->R, d_graph, d_degree);
+    note_launch();
+    if ((s = cuda_status(cudaGetLastError(), "degree"))) return s;
+  }
+  return read_err(&h->err, st);
+}
+
 pecann_status pecann_density(const pecann_dataset* ds, const int32_t* d_graph, const pecann_params* p,
                              int32_t* d_knn_ids, float* d_knn_dist, float* d_density, float* d_rank_key,
                              void* ws, size_t ws_bytes, void* stream) {

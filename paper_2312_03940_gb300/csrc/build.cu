@@ -461,7 +461,7 @@ static cudaError_t prune_reverse_batch(const DataView& dv, BuildArgs& b, int64_t
 __global__ void k_iota_fill(int64_t n, int32_t* iota, int32_t* cnt, int32_t k) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     iota[i] = (int32_t)i;
-    cnt[i] = k;
+    if (cnt) cnt[i] = k;
   }
 }
 
@@ -541,6 +541,55 @@ cudaError_t run_all_prune(const DataView& dv, int R, float alpha, const int32_t*
   b.big_cap = (int)big_cap;
   b.err = d_err;
   return prune_reverse_batch(dv, b, n, counters, st);
+}
+
+// Step 2 alone for every point, from given candidate lists (ids / dis: n x
+// K, any order, repeats allowed; cnt: valid entries per point) on an empty
+// graph: G(p) <- RobustPrune(p, list(p), alpha, R). No reverse edges. ws:
+// prune_lists_ws_bytes(n) bytes.
+size_t prune_lists_ws_bytes(int64_t n) { return ((size_t)n * 4 + 255) & ~(size_t)255; }
+
+cudaError_t run_prune_lists(const DataView& dv, int R, float alpha, const int32_t* ids, const float* dis,
+                            const int32_t* cnt, int K, int32_t* G, void* ws, int* d_err, cudaStream_t st) {
+  const int64_t n = dv.n;
+  int32_t* iota = (int32_t*)ws;
+  cudaError_t e;
+  set_where("graph prune: clear");
+  if ((e = cudaMemsetAsync(G, 0xff, (size_t)n * R * 4, st)) != cudaSuccess) return e;
+  k_iota_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8), 256, 0, st>>>(n, iota, nullptr,
+                                                                                                      0);
+  note_launch();
+  BuildArgs b;
+  memset(&b, 0, sizeof(b));
+  b.X = dv.X;
+  b.row_bytes = dv.row_bytes;
+  b.n = n;
+  b.C = dv.C;
+  b.G = G;
+  b.R = R;
+  b.a2 = alpha * alpha;
+  b.batch = iota;
+  b.m = n;
+  b.vis_ids = ids;
+  b.vis_dis = dis;
+  b.vis_cnt = cnt;
+  b.vcap = K;
+  b.cap_new = (int)pow2_size((size_t)K + R);
+  b.err = d_err;
+  const size_t new_smem_warp = (size_t)b.cap_new * 12 + (size_t)R * 8;
+  const int wpb = new_smem_warp * 4 <= 200 * 1024 ? 4 : (new_smem_warp * 2 <= 200 * 1024 ? 2 : 1);
+  return dispatch_layout(dv, [&](auto dt, auto met, auto wv, auto cpl) -> cudaError_t {
+    auto kn = k_prune_new<decltype(dt)::value, decltype(met)::value, decltype(wv)::value, decltype(cpl)::value>;
+    const size_t sm = new_smem_warp * wpb;
+    set_where("graph prune: attribute");
+    cudaError_t ee = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ee != cudaSuccess) return ee;
+    set_where("graph prune: launch");
+    const int64_t blocks = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)num_sms() * 8);
+    kn<<<(unsigned)blocks, wpb * 32, sm, st>>>(b);
+    note_launch();
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t run_build(const DataView& dv, const pecann_params& p, const int32_t* d_order, int32_t* G,

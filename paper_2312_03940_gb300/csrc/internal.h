@@ -188,6 +188,15 @@ cudaError_t run_nndescent(const DataView& fv, int K, int repeats, const int32_t*
 // Out-degrees of an n x R graph (build.cu).
 __global__ void k_degree(int64_t n, int R, const int32_t* G, int32_t* deg);
 
+// HCNNG graph index (hcnng.cu). Leaves hold at most HCNNG_MAX_LEAF points
+// (their pair keys fit in shared memory); degrees of the leaf forests at most
+// HCNNG_MAX_DEG.
+constexpr int HCNNG_MAX_LEAF = 200;
+constexpr int HCNNG_MAX_DEG = 16;
+size_t hcnng_ws_bytes(int64_t n, int repeats, int leaf, int mst_deg);
+cudaError_t run_hcnng(const DataView& fv, int repeats, int leaf, int mst_deg, float alpha, int R, uint64_t seed,
+                      int32_t* G, int64_t* h_leaves, void* ws, int* d_err, cudaStream_t st);
+
 int num_sms();
 // Counts the kernels the library launches (reported by pecann_kernel_launches).
 void note_launch();

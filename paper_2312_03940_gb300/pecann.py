@@ -54,7 +54,8 @@ class PecannClusterSetting(ctypes.Structure):
 EXPORTS = ["pecann_params_default", "pecann_status_string", "pecann_last_error", "pecann_version",
            "pecann_kernel_launches",
            "pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_nndescent_workspace_size",
-           "pecann_build_nndescent", "pecann_density", "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
+           "pecann_build_nndescent", "pecann_hcnng_workspace_size", "pecann_build_hcnng", "pecann_density",
+           "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
            "pecann_batch_prepare", "pecann_run_batched", "pecann_cluster_workspace_size", "pecann_cluster_sweep"]
 
 NOALLOC_MAX_POINTS = 1 << 20
@@ -94,6 +95,8 @@ def load_library(path: str | None = None):
     lib.pecann_build_graph.argtypes = [D, P, vp, vp, vp, vp, sz, vp]
     lib.pecann_nndescent_workspace_size.argtypes = [D, P, i32, i32, ctypes.POINTER(sz)]
     lib.pecann_build_nndescent.argtypes = [D, P, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]
+    lib.pecann_hcnng_workspace_size.argtypes = [D, P, i32, i32, i32, ctypes.POINTER(sz)]
+    lib.pecann_build_hcnng.argtypes = [D, P, i32, i32, i32, vp, vp, vp, vp, sz, vp]
     lib.pecann_density.argtypes = [D, vp, P, vp, vp, vp, vp, vp, sz, vp]
     lib.pecann_dependent_points.argtypes = [D, vp, P, vp, vp, vp, vp, vp, ctypes.POINTER(i64), vp, sz, vp]
     lib.pecann_cluster.argtypes = [i64, vp, vp, vp, P, vp, ctypes.POINTER(i64), vp, sz, vp]
@@ -102,7 +105,7 @@ def load_library(path: str | None = None):
     lib.pecann_cluster_sweep.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, ctypes.POINTER(PecannClusterSetting),
                                          vp, ctypes.POINTER(i64), vp, sz, vp]
     for f in ["pecann_workspace_size", "pecann_search", "pecann_build_graph", "pecann_nndescent_workspace_size",
-              "pecann_build_nndescent", "pecann_density",
+              "pecann_build_nndescent", "pecann_hcnng_workspace_size", "pecann_build_hcnng", "pecann_density",
               "pecann_dependent_points", "pecann_cluster", "pecann_density_noalloc", "pecann_batch_workspace_size",
               "pecann_batch_prepare", "pecann_run_batched", "pecann_cluster_workspace_size", "pecann_cluster_sweep"]:
         getattr(lib, f).restype = ctypes.c_int
@@ -254,6 +257,25 @@ def pecann_build_nndescent(ds: Dataset, p: PecannParams, K: int, init: torch.Ten
                                       _ptr(degree), _ptr(knn), ctypes.c_void_p(changes.data_ptr()),
                                       _ptr(ws), ws.numel(), _stream(stream)))
     return dict(graph=graph, degree=degree, knn=knn, changes=changes[:, :rounds].numpy())
+
+
+def pecann_build_hcnng(ds: Dataset, p: PecannParams, repeats: int, leaf_size: int, mst_deg: int,
+                       ws: torch.Tensor | None = None, stream=None):
+    """HCNNG graph index (p.R, p.alpha, p.seed). Returns dict graph (n,R),
+    degree (n,) int32 and leaves (repeats,) int64 on the host."""
+    lib = load_library()
+    if ws is None:
+        nb = ctypes.c_size_t(0)
+        _check(lib.pecann_hcnng_workspace_size(ds.ref, ctypes.byref(p), repeats, leaf_size, mst_deg,
+                                               ctypes.byref(nb)))
+        ws = torch.empty(nb.value, dtype=torch.uint8, device=ds.X.device)
+    dev = ds.X.device
+    graph = torch.empty((ds.n, p.R), dtype=torch.int32, device=dev)
+    degree = torch.empty(ds.n, dtype=torch.int32, device=dev)
+    leaves = torch.zeros(repeats, dtype=torch.int64)  # host
+    _check(lib.pecann_build_hcnng(ds.ref, ctypes.byref(p), repeats, leaf_size, mst_deg, _ptr(graph), _ptr(degree),
+                                  ctypes.c_void_p(leaves.data_ptr()), _ptr(ws), ws.numel(), _stream(stream)))
+    return dict(graph=graph, degree=degree, leaves=leaves.numpy())
 
 
 def pecann_density(ds: Dataset, graph: torch.Tensor, p: PecannParams, ws: torch.Tensor | None = None,

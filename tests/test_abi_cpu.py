@@ -153,3 +153,19 @@ def test_nndescent_checks_on_host(lib):
     bad = pc.params(R=24, alpha=0.9)
     assert call(ctypes.byref(ds), ctypes.byref(bad), 16, 1, g, 5, g, None, None, None, g, 1 << 40, None) == pc.EINVAL
     assert call(ctypes.byref(ds), ctypes.byref(p), 16, 1, g, 5, g, None, None, None, g, 64, None) == pc.ENOMEM
+
+
+def test_hcnng_checks_on_host(lib):
+    """HCNNG workspace sizing and argument checks answer on the host."""
+    p = pc.params(R=32, alpha=1.2)
+    ds = pc.PecannDataset(256, 100_000, 128, pc.U8, pc.L2, 0, None, None)
+    b = ctypes.c_size_t(0)
+    assert lib.pecann_hcnng_workspace_size(ctypes.byref(ds), ctypes.byref(p), 3, 200, 3, ctypes.byref(b)) == pc.OK
+    assert b.value >= 100_000 * (4 * 4 + 2 * 9 * 4)  # orders, flags and both candidate arrays
+    for reps, leaf, deg in ((0, 200, 3), (3, 201, 3), (3, 1, 3), (3, 200, 17)):
+        assert lib.pecann_hcnng_workspace_size(ctypes.byref(ds), ctypes.byref(p), reps, leaf, deg,
+                                               ctypes.byref(b)) == pc.EINVAL
+    g = ctypes.c_void_p(256)
+    call = lib.pecann_build_hcnng
+    assert call(ctypes.byref(ds), ctypes.byref(p), 3, 200, 3, None, None, None, g, 1 << 40, None) == pc.EINVAL
+    assert call(ctypes.byref(ds), ctypes.byref(p), 3, 200, 3, g, None, None, g, 64, None) == pc.ENOMEM
