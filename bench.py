@@ -166,7 +166,7 @@ def replica_throughput(points_per_rank: int, steps: int, world: int, elapsed_s: 
 # the sources each profiled kernel is built from: a profile's counters stand
 # for the kernel only while these files are unchanged
 KERNEL_SOURCES = {
-    "k_bf_screen": ["bf_screen.cu", "tcgen05.cuh", "common.cuh", "internal.h"],
+    "k_bf_screen": ["bf_screen.cu", "tcgen05.cuh", "common.cuh"],
     "k_search": ["search.cu", "search_kernel.cuh", "search_common.cuh", "search_u8.cu", "search_f32.cu",
                  "search_f32ip.cu", "search_bf16.cu", "search_fp8.cu", "dispatch.cuh", "common.cuh", "internal.h"],
 }
