@@ -388,33 +388,21 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
         tc::fence_after_sync();
 #pragma unroll 1
         for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 32) {
-          // the chunk's per-column inputs (squared norms for L2, rank keys
-          // for the dependent pass; padded past n, read four at a time through
-          // L1, the same addresses for the whole warp) are fetched before the
-          // TMEM load, whose wait would otherwise hold them back
-          float4 nn4[8], rk4[8];
-          if (METRIC == MET_L2) {
-            const float4* m4 = reinterpret_cast<const float4*>(a.pnorm2 + j0 + c0);
-#pragma unroll
-            for (int q = 0; q < 8; q++) nn4[q] = __ldg(m4 + q);
-          }
-          if (MODE == SCR_DEP) {
-            const float4* k4 = reinterpret_cast<const float4*>(a.rank_key + j0 + c0);
-#pragma unroll
-            for (int q = 0; q < 8; q++) rk4[q] = __ldg(k4 + q);
-          }
           float v[32];
           tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * SC_N + c0), v);
           // approximate keys, smaller = closer: -<x, y> (IP), |y|^2 - 2 <x, y>
-          // (L2); the chunk's best key by a tree of depth 5
+          // (L2: the squared norms, padded past n, read four at a time
+          // through L1, the same addresses for the whole warp); the chunk's
+          // best key by a tree of depth 5
           if (MODE == SCR_DEP) {
             // only points ranked above the query count: the others get the
             // worst key (rank keys padded past n with NaN, never above)
+            const float4* k4 = reinterpret_cast<const float4*>(a.rank_key + j0 + c0);
             // (as a product: -inf, which gives key +inf under both metrics)
             const float worst = -INFINITY;
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-              const float4 kk = rk4[q];
+              const float4 kk = __ldg(k4 + q);
               const float kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
               for (int u = 0; u < 4; u++) {
@@ -425,9 +413,10 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
           }
           float w[16];
           if (METRIC == MET_L2) {
+            const float4* m4 = reinterpret_cast<const float4*>(a.pnorm2 + j0 + c0);
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-              const float4 nn = nn4[q];
+              const float4 nn = __ldg(m4 + q);
               // a masked column carries -inf as its product: its key is +inf
               v[4 * q + 0] = __fmaf_rn(-2.0f, v[4 * q + 0], nn.x);
               v[4 * q + 1] = __fmaf_rn(-2.0f, v[4 * q + 1], nn.y);
