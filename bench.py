@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--graph-line-only", action="store_true",
                     help="u8-1m / vmf1024-graph: the Vamana FP32 (or uint8) graph line alone, without CPU baseline, "
                          "e2e or recall (for short profiling runs)")
+    ap.add_argument("--exact-line-only", action="store_true",
+                    help="u8-1m: the exact-index line alone, without CPU baseline or recall (profiling runs)")
     ap.add_argument("--workload", default="vmf1024",
                     choices=["vmf1024", "vmf1024-graph", "u8-1m", "batched64", "sphere384"],
                     help="vmf1024: the benchmark line (with its variants); vmf1024-graph / u8-1m: report lines alone")
@@ -587,6 +589,12 @@ def u8_variants(args, dev, stream, threads):
     X, gt = u8_data(n)
     Xd = torch.from_numpy(X).to(dev)
     ds = pc.Dataset(Xd)
+    if args.exact_line_only:
+        pb = pc.params(k=U8["k"], center=pc.CENTER_PRODUCT, n_clusters=U8["n_clusters"], index=pc.INDEX_BRUTE_FORCE)
+        path = Path(ds, None, pb, dev)
+        el, dms = timed(path.step, 1, args.variant_steps, stream)
+        return [{"metric": METRIC, "value": n / (el / args.variant_steps), "unit": UNIT, "dtype": "u8",
+                 "ms_per_step": el * 1000 / args.variant_steps, "density_ms": dms, "index": "brute force"}]
     p = pc.params(k=U8["k"], R=U8["R"], L_build=U8["L_build"], L_search=U8["L"], L_dep=U8["L"], alpha=U8["alpha"],
                   n_start=min(n, U8["n_start"]), build_passes=U8["build_passes"], center=pc.CENTER_PRODUCT,
                   n_clusters=U8["n_clusters"])
