@@ -387,35 +387,36 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
         }
         tc::fence_after_sync();
 #pragma unroll 1
-        for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 32) {
-          float v[32];
-          tc::tmem_ld32(tmem + lane_addr + (uint32_t)(b * SC_N + c0), v);
+        for (int c00 = 128 * half; c00 < 128 * half + 128; c00 += 64) {
+          // 64 columns per TMEM load, taken as two 32-column chunks whose
+          // minima are formed before either is taken apart (two independent
+          // chains for the scheduler)
+          float v[64];
+          tc::tmem_ld64(tmem + lane_addr + (uint32_t)(b * SC_N + c00), v);
           // approximate keys, smaller = closer: -<x, y> (IP), |y|^2 - 2 <x, y>
           // (L2: the squared norms, padded past n, read four at a time
-          // through L1, the same addresses for the whole warp); the chunk's
-          // best key by a tree of depth 5
+          // through L1, the same addresses for the whole warp)
           if (MODE == SCR_DEP) {
             // only points ranked above the query count: the others get the
             // worst key (rank keys padded past n with NaN, never above)
-            const float4* k4 = reinterpret_cast<const float4*>(a.rank_key + j0 + c0);
+            const float4* k4 = reinterpret_cast<const float4*>(a.rank_key + j0 + c00);
             // (as a product: -inf, which gives key +inf under both metrics)
             const float worst = -INFINITY;
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
+            for (int q = 0; q < 16; q++) {
               const float4 kk = __ldg(k4 + q);
               const float kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
               for (int u = 0; u < 4; u++) {
-                const int32_t j = (int32_t)(j0 + c0 + 4 * q + u);
+                const int32_t j = (int32_t)(j0 + c00 + 4 * q + u);
                 if (!rank_above_key(kv[u], j, qkey, qid)) v[4 * q + u] = worst;
               }
             }
           }
-          float w[16];
           if (METRIC == MET_L2) {
-            const float4* m4 = reinterpret_cast<const float4*>(a.pnorm2 + j0 + c0);
+            const float4* m4 = reinterpret_cast<const float4*>(a.pnorm2 + j0 + c00);
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
+            for (int q = 0; q < 16; q++) {
               const float4 nn = __ldg(m4 + q);
               // a masked column carries -inf as its product: its key is +inf
               v[4 * q + 0] = __fmaf_rn(-2.0f, v[4 * q + 0], nn.x);
@@ -423,43 +424,51 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
               v[4 * q + 2] = __fmaf_rn(-2.0f, v[4 * q + 2], nn.z);
               v[4 * q + 3] = __fmaf_rn(-2.0f, v[4 * q + 3], nn.w);
             }
+          }
+          // each chunk's best key by a tree of depth 5
+          float best[2];
 #pragma unroll
-            for (int t = 0; t < 16; t++) w[t] = fminf(v[t], v[t + 16]);
-          } else {
+          for (int sub = 0; sub < 2; sub++) {
+            float w[16];
 #pragma unroll
-            for (int t = 0; t < 16; t++) w[t] = fmaxf(v[t], v[t + 16]);
+            for (int t = 0; t < 16; t++)
+              w[t] = METRIC == MET_L2 ? fminf(v[32 * sub + t], v[32 * sub + t + 16])
+                                      : fmaxf(v[32 * sub + t], v[32 * sub + t + 16]);
+#pragma unroll
+            for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+              for (int t = 0; t < h; t++) w[t] = METRIC == MET_L2 ? fminf(w[t], w[t + h]) : fmaxf(w[t], w[t + h]);
+            best[sub] = METRIC == MET_L2 ? w[0] : -w[0];
           }
 #pragma unroll
-          for (int h = 8; h >= 1; h >>= 1)
+          for (int sub = 0; sub < 2; sub++) {
+            if (!(PASS == SCR_COLLECT ? (best[sub] <= thr) : (best[sub] < thr))) continue;  // the common case
+            // the columns that beat the threshold, then one at a time (a
+            // compact loop: the key of column t is picked by selects)
+            uint32_t hm = 0;
 #pragma unroll
-            for (int t = 0; t < h; t++) w[t] = METRIC == MET_L2 ? fminf(w[t], w[t + h]) : fmaxf(w[t], w[t + h]);
-          const float best = METRIC == MET_L2 ? w[0] : -w[0];
-          if (!(PASS == SCR_COLLECT ? (best <= thr) : (best < thr))) continue;  // the common case
-          // the columns that beat the threshold, then one at a time (a
-          // compact loop: the key of column t is picked by selects)
-          uint32_t hm = 0;
+            for (int t = 0; t < 32; t++) {
+              const float key = METRIC == MET_L2 ? v[32 * sub + t] : -v[32 * sub + t];
+              hm |= (uint32_t)(PASS == SCR_COLLECT ? (key <= thr) : (key < thr)) << t;
+            }
+            const int64_t jbase = j0 + c00 + 32 * sub;
+            if (jbase + 32 > a.n) hm &= jbase >= a.n ? 0u : (0xffffffffu >> (32 - (int)(a.n - jbase)));
+            if (qid >= jbase && qid < jbase + 32) hm &= ~(1u << (qid - jbase));
+            while (hm) {
+              const int t = __ffs(hm) - 1;
+              hm &= hm - 1;
+              float key = v[32 * sub];
 #pragma unroll
-          for (int t = 0; t < 32; t++) {
-            const float key = METRIC == MET_L2 ? v[t] : -v[t];
-            hm |= (uint32_t)(PASS == SCR_COLLECT ? (key <= thr) : (key < thr)) << t;
-          }
-          const int64_t jbase = j0 + c0;
-          if (jbase + 32 > a.n) hm &= jbase >= a.n ? 0u : (0xffffffffu >> (32 - (int)(a.n - jbase)));
-          if (qid >= jbase && qid < jbase + 32) hm &= ~(1u << (qid - jbase));
-          while (hm) {
-            const int t = __ffs(hm) - 1;
-            hm &= hm - 1;
-            float key = v[0];
-#pragma unroll
-            for (int i = 1; i < 32; i++) key = t == i ? v[i] : key;
-            if (METRIC != MET_L2) key = -key;
-            const int32_t j = (int32_t)(jbase + t);
-            if (PASS == SCR_COLLECT) {
-              const int slot = atomicAdd(&row_cnt[rl], 1);
-              if (slot < a.cap) a.out_ids[r * a.cap + slot] = j;
-            } else if (key < thr) {  // thr may have dropped since the mask
-              heap_push(hk, hi, et, cnt, key, j);
-              if (cnt == SC_HALF) thr = hk[et];
+              for (int i = 1; i < 32; i++) key = t == i ? v[32 * sub + i] : key;
+              if (METRIC != MET_L2) key = -key;
+              const int32_t j = (int32_t)(jbase + t);
+              if (PASS == SCR_COLLECT) {
+                const int slot = atomicAdd(&row_cnt[rl], 1);
+                if (slot < a.cap) a.out_ids[r * a.cap + slot] = j;
+              } else if (key < thr) {  // thr may have dropped since the mask
+                heap_push(hk, hi, et, cnt, key, j);
+                if (cnt == SC_HALF) thr = hk[et];
+              }
             }
           }
         }
