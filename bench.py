@@ -562,7 +562,8 @@ def vmf_graph_variants(args, X, Xd, exact_dist, exact_labels, dev, stream, threa
                                                           f"(build: {VMF['build_passes']} passes, beam {VMF['L_build']}, "
                                                           f"{p.n_start} start points)",
                            "traversal": tag + ("" if tag == "fp32" else " rows, exact FP32 re-rank")},
-                "density_ms": dms, "build_s": build_s,
+                "density_ms": dms, "build_s": build_s, "dep_rounds": int(path.stats[0]),
+                "unfinished_after_round0": int(path.stats[1]), "brute_force_tail": int(path.stats[63]),
                 "recall_full_n_vs_exact_index": full_recall(got, exact_dist),
                 "ari_vs_exact_index": exact.ari(path.labels.cpu().numpy(), exact_labels),
                 "below_recall_bar": True,
