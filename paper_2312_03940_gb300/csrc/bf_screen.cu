@@ -61,7 +61,6 @@ constexpr int SC_EPI = 256;        // epilogue threads (8 warps)
 constexpr int SC_THREADS = 64 + SC_EPI;
 constexpr uint32_t SC_A_BYTES = SC_M * SC_KCH * 2;   // 16 KB
 constexpr uint32_t SC_B_BYTES = SC_N * SC_KCH * 2;   // 32 KB
-constexpr uint32_t SC_STAGE_BYTES = SC_A_BYTES + SC_B_BYTES;
 constexpr uint64_t SC_WAIT_NS = 2000000000ull;       // 2 s per wait
 
 constexpr int SC_CAP = 1024;       // collect pass: candidates per overflowed query
@@ -229,14 +228,30 @@ __device__ __forceinline__ bool pace_enter(const ScreenArgs& a, int64_t epoch, i
 // stage's empty barrier in every CTA of the cluster). A CTA whose query tile
 // lies past the last one still takes part, on rows that read as zeros and
 // produce no output.
+// Per cluster size: CL = 2 runs the pair form (one M = 256 MMA per CTA pair,
+// each CTA holding its 128 query rows and half of the 256 point rows of a
+// stage, so a stage is 32 KB and four fit); CL = 1 and 4 hold the whole
+// point tile in each CTA.
+template <int CL>
+struct ScLayout {
+  static constexpr bool PAIR = CL == 2;
+  static constexpr int STAGES = PAIR ? 4 : SC_STAGES;
+  static constexpr uint32_t B_BYTES = PAIR ? SC_B_BYTES / 2 : SC_B_BYTES;
+  static constexpr uint32_t STAGE_BYTES = SC_A_BYTES + B_BYTES;
+};
+
 template <int MODE, int PASS, int METRIC, int CL>
 __global__ void __launch_bounds__(SC_THREADS, 1)
     k_bf_screen(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, ScreenArgs a) {
+  using L = ScLayout<CL>;
+  constexpr bool PAIR = L::PAIR;
+  constexpr int STAGES = L::STAGES;
+  constexpr uint32_t STAGE_BYTES = L::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* hk = reinterpret_cast<float*>(ring + SC_STAGES * SC_STAGE_BYTES);  // [SC_HALF][SC_EPI]
-  int32_t* hi = reinterpret_cast<int32_t*>(hk + SC_HALF * SC_EPI);          // [SC_HALF][SC_EPI]
-  __shared__ __align__(8) uint64_t full_bar[SC_STAGES], empty_bar[SC_STAGES];
+  float* hk = reinterpret_cast<float*>(ring + STAGES * STAGE_BYTES);       // [SC_HALF][SC_EPI]
+  int32_t* hi = reinterpret_cast<int32_t*>(hk + SC_HALF * SC_EPI);         // [SC_HALF][SC_EPI]
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], final_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -254,21 +269,29 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int s = 0; s < SC_STAGES; s++) {
+    for (int s = 0; s < STAGES; s++) {
+      // pair: full_bar of the even CTA counts both CTAs' bytes; every MMA
+      // commit arrives once on each CTA's empty_bar
       tc::mbar_init(&full_bar[s], 1);
-      tc::mbar_init(&empty_bar[s], CL);
+      tc::mbar_init(&empty_bar[s], PAIR ? 1 : CL);
     }
     for (int b = 0; b < 2; b++) {
       tc::mbar_init(&tfull_bar[b], 1);
-      tc::mbar_init(&tempty_bar[b], SC_EPI);
+      // pair: the even CTA's barrier takes the epilogue threads of both CTAs
+      tc::mbar_init(&tempty_bar[b], PAIR ? 2 * SC_EPI : SC_EPI);
     }
     tc::mbar_init(&final_bar, 1);
     tc::fence_mbar_init();
   }
   if (threadIdx.x < SC_M) row_cnt[threadIdx.x] = 0;
   if (warp == 1) {
-    tc::tmem_alloc(&tmem_slot, 2 * SC_N);
-    tc::tmem_relinquish();
+    if constexpr (PAIR) {
+      tc::tmem_alloc_pair(&tmem_slot, 2 * SC_N);
+      tc::tmem_relinquish_pair();
+    } else {
+      tc::tmem_alloc(&tmem_slot, 2 * SC_N);
+      tc::tmem_relinquish();
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -293,35 +316,48 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
           if (pacing && pt % a.pace_every == 0)
             pacing = pace_enter(a, round * epr + pt / a.pace_every, epr, groups, CL);
           for (int c = 0; c < a.kc; c++) {
-            const int s = (int)(it % SC_STAGES);
-            const uint32_t ph = (uint32_t)((it / SC_STAGES) & 1);
+            const int s = (int)(it % STAGES);
+            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
             if (!tc::mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, SC_WAIT_NS)) {
               ok = false;
               break;
             }
-            uint8_t* st = ring + (size_t)s * SC_STAGE_BYTES;
-            tc::mbar_arrive_expect_tx(&full_bar[s], SC_STAGE_BYTES);
-            tc::tma_load_2d(st, &ta, c * SC_KCH, (int32_t)(qt * SC_M), &full_bar[s]);
-            if (CL == 1)
-              tc::tma_load_2d(st + SC_A_BYTES, &tb, c * SC_KCH, (int32_t)(pt * SC_N), &full_bar[s]);
-            else
-              tc::tma_load_2d_mc(st + SC_A_BYTES + crank * (SC_B_BYTES / CL), &tb, c * SC_KCH,
-                                 (int32_t)(pt * SC_N + crank * (SC_N / CL)), &full_bar[s], cl_mask);
+            uint8_t* st = ring + (size_t)s * STAGE_BYTES;
+            if constexpr (PAIR) {
+              // both CTAs' loads complete on the even CTA's full barrier
+              const uint32_t fb = tc::mapa(tc::smem_u32(&full_bar[s]), 0);
+              if (crank == 0) tc::mbar_arrive_expect_tx(&full_bar[s], 2 * STAGE_BYTES);
+              tc::tma_load_2d_pair(st, &ta, c * SC_KCH, (int32_t)(qt * SC_M), fb);
+              tc::tma_load_2d_pair(st + SC_A_BYTES, &tb, c * SC_KCH, (int32_t)(pt * SC_N + crank * (SC_N / 2)), fb);
+            } else {
+              tc::mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+              tc::tma_load_2d(st, &ta, c * SC_KCH, (int32_t)(qt * SC_M), &full_bar[s]);
+              if (CL == 1)
+                tc::tma_load_2d(st + SC_A_BYTES, &tb, c * SC_KCH, (int32_t)(pt * SC_N), &full_bar[s]);
+              else
+                tc::tma_load_2d_mc(st + SC_A_BYTES + crank * (SC_B_BYTES / CL), &tb, c * SC_KCH,
+                                   (int32_t)(pt * SC_N + crank * (SC_N / CL)), &full_bar[s], cl_mask);
+            }
             it++;
           }
         }
       }
       // loads still in flight land before the block exits: wait for the last
-      // SC_STAGES issued loads (bounded, whatever the abort flag says)
+      // STAGES issued loads (bounded, whatever the abort flag says); in the
+      // pair the even CTA's barriers count the odd CTA's loads too, and the
+      // final cluster barrier holds the odd CTA until then
       int no_abort = 0;
-      for (uint64_t j = it > SC_STAGES ? it - SC_STAGES : 0; j < it; j++)
-        tc::mbar_wait(&full_bar[j % SC_STAGES], (uint32_t)((j / SC_STAGES) & 1), &no_abort, SC_WAIT_NS);
+      if (!PAIR || crank == 0)
+        for (uint64_t j = it > STAGES ? it - STAGES : 0; j < it; j++)
+          tc::mbar_wait(&full_bar[j % STAGES], (uint32_t)((j / STAGES) & 1), &no_abort, SC_WAIT_NS);
       if (!ok) set_error(a.err, ERR_TIMEOUT);
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(SC_M, SC_N);
+    if (PAIR && crank != 0) {
+      // the odd CTA of a pair issues nothing (see the end of the kernel)
+    } else if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(PAIR ? 2 * SC_M : SC_M, SC_N);
       uint64_t it = 0, tile = 0;
       bool ok = true;
       for (int64_t g = cl_id; g * CL < n_qt && ok; g += n_cl) {
@@ -334,26 +370,41 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
           tc::fence_after_sync();
           const uint32_t dacc = tmem + (uint32_t)(b * SC_N);
           for (int c = 0; c < a.kc; c++, it++) {
-            const int s = (int)(it % SC_STAGES);
-            if (!tc::mbar_wait(&full_bar[s], (uint32_t)((it / SC_STAGES) & 1), &abort_flag, SC_WAIT_NS)) {
+            const int s = (int)(it % STAGES);
+            if (!tc::mbar_wait(&full_bar[s], (uint32_t)((it / STAGES) & 1), &abort_flag, SC_WAIT_NS)) {
               ok = false;
               break;
             }
             tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(ring + (size_t)s * SC_STAGE_BYTES), sb = sa + SC_A_BYTES;
+            const uint32_t sa = tc::smem_u32(ring + (size_t)s * STAGE_BYTES), sb = sa + SC_A_BYTES;
 #pragma unroll
-            for (int k = 0; k < SC_KCH / 16; k++)
-              tc::mma_bf16(dacc, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k), idesc, (c | k) != 0);
-            if (CL == 1)
+            for (int k = 0; k < SC_KCH / 16; k++) {
+              if constexpr (PAIR)
+                tc::mma_bf16_pair(dacc, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k), idesc,
+                                  (c | k) != 0);
+              else
+                tc::mma_bf16(dacc, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k), idesc, (c | k) != 0);
+            }
+            if constexpr (PAIR)
+              tc::mma_commit_pair(&empty_bar[s], cl_mask);
+            else if (CL == 1)
               tc::mma_commit(&empty_bar[s]);
             else
               tc::mma_commit_mc(&empty_bar[s], cl_mask);
           }
-          if (ok) tc::mma_commit(&tfull_bar[b]);
+          if (ok) {
+            if constexpr (PAIR)
+              tc::mma_commit_pair(&tfull_bar[b], cl_mask);
+            else
+              tc::mma_commit(&tfull_bar[b]);
+          }
         }
       }
       // every MMA this thread issued completes before TMEM is released
-      tc::mma_commit(&final_bar);
+      if constexpr (PAIR)
+        tc::mma_commit_pair(&final_bar, cl_mask);
+      else
+        tc::mma_commit(&final_bar);
       int no_abort = 0;
       tc::mbar_wait(&final_bar, 0, &no_abort, SC_WAIT_NS);
       if (!ok) set_error(a.err, ERR_TIMEOUT);
@@ -473,7 +524,10 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
           }
         }
         tc::fence_before_sync();
-        tc::mbar_arrive(&tempty_bar[b]);
+        if (PAIR && crank != 0)
+          tc::mbar_arrive_cluster(tc::mapa(tc::smem_u32(&tempty_bar[b]), 0));
+        else
+          tc::mbar_arrive(&tempty_bar[b]);
       }
       // the decision to give up is made uniform over the epilogue threads
       // (a thread that left the loop early reaches this barrier too)
@@ -534,11 +588,20 @@ __global__ void __launch_bounds__(SC_THREADS, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (PAIR && crank != 0 && threadIdx.x == 32) {
+    // the odd CTA's TMEM is released only after the even CTA's last commit:
+    // every MMA that writes it has completed
+    int no_abort = 0;
+    tc::mbar_wait(&final_bar, 0, &no_abort, SC_WAIT_NS);
+  }
   // no CTA leaves while a peer may still write into its shared memory
   if (CL > 1) tc::cluster_sync();
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 2 * SC_N);
+    if constexpr (PAIR)
+      tc::tmem_dealloc_pair(tmem, 2 * SC_N);
+    else
+      tc::tmem_dealloc(tmem, 2 * SC_N);
   }
 }
 
@@ -653,8 +716,9 @@ static cudaError_t make_map(CUtensorMap* m, const void* base, int64_t n, int d, 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+template <int CL>
 static size_t screen_smem() {
-  return 1024 + (size_t)SC_STAGES * SC_STAGE_BYTES + 2 * (size_t)SC_HALF * SC_EPI * 4;
+  return 1024 + (size_t)ScLayout<CL>::STAGES * ScLayout<CL>::STAGE_BYTES + 2 * (size_t)SC_HALF * SC_EPI * 4;
 }
 
 constexpr int64_t SC_PACE_MAX = 65536;  // entries of the pacing counters
@@ -664,7 +728,7 @@ static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int
                                    cudaStream_t st) {
   ScreenArgs a = a_in;
   auto kern = k_bf_screen<MODE, PASS, METRIC, CL>;
-  const size_t smem = screen_smem();
+  const size_t smem = screen_smem<CL>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
     set_where("brute-force screen: shared-memory attribute");

@@ -136,11 +136,23 @@ __device__ __forceinline__ void keep_keys(WarpSmem& w, bool has, uint64_t key, u
   m += __popc(mk);
 }
 
+template <bool PACK>
+__device__ __forceinline__ void put_key(WarpSmem& w, bool has, uint64_t key, int c, uint64_t worst, int& m,
+                                        unsigned lt) {
+  if constexpr (PACK)
+    keep_keys(w, has, key, worst, m, lt);
+  else if (has)
+    w.ckeys[c] = key;
+}
+
 // Keys (canonical distance to the query, id) of the staged candidates; the
 // ones below `worst` are packed at the front of ckeys (in no particular
 // order) and their number is returned. With worst = KEY_NONE every key is
 // kept.
-template <int DT, int METRIC, int W, int CPL, int QC>
+// PACK (layouts of 4 or 8 lanes per row, several keys per pass): keys are
+// filtered and packed as they are made; otherwise (one or two keys per pass)
+// key c goes to ckeys[c], all nc of them, and nc is returned.
+template <int DT, int METRIC, int W, int CPL, int QC, bool PACK = (W <= 8)>
 __device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int nc, const uint4 (&qv)[QC],
                                           int lane, uint64_t worst = KEY_NONE) {
   constexpr int GR = 32 / W;
@@ -170,7 +182,7 @@ __device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int 
         k += __shfl_xor_sync(FULL, k, 2);
         k += __shfl_xor_sync(FULL, k, 1);
         const bool has = gl == 0 && c < nc;
-        keep_keys(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, worst, m, lt);
+        put_key<PACK>(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, c, worst, m, lt);
         break;
       }
     }
@@ -209,8 +221,8 @@ __device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int 
         }
         const int c = c0 + u * GR + g, c1 = c + GR;
         const bool h0 = gl == 0 && c < nc, h1 = gl == 0 && c1 < nc;
-        keep_keys(w, h0, h0 ? make_key(s.x, w.cids[c]) : KEY_NONE, worst, m, lt);
-        keep_keys(w, h1, h1 ? make_key(s.y, w.cids[c1]) : KEY_NONE, worst, m, lt);
+        put_key<PACK>(w, h0, h0 ? make_key(s.x, w.cids[c]) : KEY_NONE, c, worst, m, lt);
+        put_key<PACK>(w, h1, h1 ? make_key(s.y, w.cids[c1]) : KEY_NONE, c1, worst, m, lt);
       }
     } else if constexpr (DT == DT_U8 && UNR == 2) {
       // the same for two rows per lane group: one split step, then plain
@@ -224,7 +236,7 @@ __device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int 
       for (int off = W / 4; off >= 1; off >>= 1) k += __shfl_xor_sync(FULL, k, off);
       const int c = c0 + (int)b * GR + g;
       const bool has = (gl & (W / 2 - 1)) == 0 && c < nc;
-      keep_keys(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, worst, m, lt);
+      put_key<PACK>(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, c, worst, m, lt);
     } else if constexpr (DT == DT_U8 && UNR == 4) {
       // integer partials, exact in any order: reduce the group's four rows
       // together. The first two steps halve the rows a lane carries (it keeps
@@ -243,7 +255,7 @@ __device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int 
       for (int off = W / 8; off >= 1; off >>= 1) k += __shfl_xor_sync(FULL, k, off);
       const int c = c0 + (2 * (int)b2 + (int)b1) * GR + g;
       const bool has = (gl & (W / 4 - 1)) == 0 && c < nc;
-      keep_keys(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, worst, m, lt);
+      put_key<PACK>(w, has, has ? make_key_nonneg((float)k, w.cids[c]) : KEY_NONE, c, worst, m, lt);
     } else {
 #pragma unroll
       for (int u = 0; u < UNR; u++) {
@@ -252,12 +264,12 @@ __device__ __forceinline__ int eval_cands(const SearchArgs& a, WarpSmem& w, int 
         const bool has = gl == 0 && c < nc;
         uint64_t key = KEY_NONE;
         if (has) key = METRIC == MET_L2 ? make_key_nonneg(dv, w.cids[c]) : make_key(dv, w.cids[c]);
-        keep_keys(w, has, key, worst, m, lt);
+        put_key<PACK>(w, has, key, c, worst, m, lt);
       }
     }
   }
   __syncwarp();
-  return m;
+  return PACK ? m : nc;
 }
 
 // Number of entries of the sorted clean keys s[0..m) below x.
@@ -426,9 +438,14 @@ __device__ __forceinline__ int merge_cands(WarpSmem& w, int& nb, int Lw, int nc,
 template <int DT, int METRIC, int W, int CPL, int QC>
 __device__ __forceinline__ int eval_merge(const SearchArgs& a, WarpSmem& w, int nc, const uint4 (&qv)[QC],
                                           int lane, int& nb, int Lw, int& cursor) {
-  const uint64_t worst = nb >= Lw ? key_clean(w.beam[Lw - 1]) : KEY_NONE;
-  const int m = eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane, worst);
-  return merge_filtered(w, nb, Lw, m, cursor, lane);
+  if constexpr (W <= 8) {
+    const uint64_t worst = nb >= Lw ? key_clean(w.beam[Lw - 1]) : KEY_NONE;
+    const int m = eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane, worst);
+    return merge_filtered(w, nb, Lw, m, cursor, lane);
+  } else {
+    eval_cands<DT, METRIC, W, CPL>(a, w, nc, qv, lane);
+    return merge_cands(w, nb, Lw, nc, cursor, lane);
+  }
 }
 
 // Merge the m candidate keys at the front of ckeys (all better than the

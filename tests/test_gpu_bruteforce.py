@@ -48,9 +48,9 @@ def gpu_path(X, metric, p):
     return out
 
 
-def check_against_oracle(X, metric, k, n_clusters, density=pc.DENS_KTH, Ld=32):
+def check_against_oracle(X, metric, k, n_clusters, density=pc.DENS_KTH, Ld=32, cl=0):
     p = pc.params(k=k, R=8, L_search=max(k, 8), L_dep=Ld, index=pc.INDEX_BRUTE_FORCE, center=pc.CENTER_PRODUCT,
-                  n_clusters=n_clusters, density=density)
+                  n_clusters=n_clusters, density=density, block_warps=cl)
     r = gpu_path(X, metric, p)
     P = oracle.Points(X, metric=metric)
     o = oracle.knn_density(P, None, L=0, k=k, density=density)
@@ -79,6 +79,18 @@ def test_ip_unit_norm_1024():
     qs = synth.sample_ids(len(X), 300, seed=202)
     _, ex = exact.exact_knn_queries(X, qs, 16, metric=exact.IP)
     assert exact.knn_recall(r["knn_dist"][qs], ex) == 1.0
+
+
+@pytest.mark.parametrize("cl", [1, 2, 4])
+def test_cluster_forms(cl):
+    """The screen's k-NN pass run by single CTAs, by CTA pairs issuing one
+    256-row MMA (each CTA holding half of every point tile) and by clusters
+    of 4 sharing point tiles by multicast: the same exact results. An odd
+    number of query tiles leaves one pair with a CTA past the last tile."""
+    X, _ = synth.vmf_like(n=2 * 128 + 77, d=256, components=6, seed=209)
+    check_against_oracle(X, pc.IP, k=12, n_clusters=6, cl=cl)
+    U, _ = synth.u8_mixture(n=2500, d=128, components=8, seed=210)
+    check_against_oracle(U, pc.L2, k=10, n_clusters=8, cl=cl)
 
 
 def test_u8_l2_128():
