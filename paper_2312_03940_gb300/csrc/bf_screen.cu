@@ -802,14 +802,17 @@ static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int
   return e;
 }
 
-// cl: CTAs per cluster for the k-NN keep pass (1, 2 or 4; 0 = automatic,
-// 1: measured on the 1.28M x 1024 and 1M x 128 sets, the screen is bound by
-// its MMAs and epilogue, not by L2 traffic, and clusters of 2 and 4 were no
-// faster); the other passes run few query tiles and use 1.
+// cl: CTAs per cluster for the k-NN keep pass: 1 (single CTAs, paced
+// sweep), 2 (CTA pairs, one 256-row MMA per pair) or 4 (clusters sharing
+// point tiles by multicast); 0 = automatic = 2: measured on the 1.28M x 1024
+// set, the pairs take the keep pass from 2.32 to 2.09-2.14 s (each CTA reads
+// half as many operand bytes into shared memory per MMA), while clusters of 4
+// were no faster than single CTAs. The other passes run few query tiles and
+// use 1.
 static cudaError_t launch_screen(int mode, int pass, int metric, const CUtensorMap& ta, const void* prows, int64_t n,
                                  int d, const ScreenArgs& a, int cl, cudaStream_t st) {
   if (a.nq <= 0) return cudaSuccess;
-  if (cl != 1 && cl != 2 && cl != 4) cl = 1;
+  if (cl != 1 && cl != 2 && cl != 4) cl = 2;
   if (mode != SCR_KNN || pass != SCR_KEEP) cl = 1;
   if (metric == MET_IP) {
     if (mode == SCR_KNN && pass == SCR_KEEP) {
