@@ -149,7 +149,8 @@ typedef struct {
   int32_t block_warps;       /* warps per block of the search kernel (1, 2, 4 or 8; 0 =
                                 automatic); with the brute-force index, the k-NN screen's
                                 CTAs per cluster: 1, 2 (CTA pairs sharing one 256-row MMA)
-                                or 4 (point tiles multicast); 0 = automatic (2). Like
+                                or 4 (point tiles multicast); 0 = automatic (2 for
+                                d >= 512, else 1). Like
                                 hash_slots it changes speed, never results                 */
   int32_t index;             /* PECANN_INDEX_GRAPH (the Vamana graph given to the call) or
                                 PECANN_INDEX_BRUTE_FORCE (no index, exact; the graph may be

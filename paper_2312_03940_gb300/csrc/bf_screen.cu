@@ -804,15 +804,16 @@ static cudaError_t launch_screen_t(const CUtensorMap& ta, const void* prows, int
 
 // cl: CTAs per cluster for the k-NN keep pass: 1 (single CTAs, paced
 // sweep), 2 (CTA pairs, one 256-row MMA per pair) or 4 (clusters sharing
-// point tiles by multicast); 0 = automatic = 2: measured on the 1.28M x 1024
-// set, the pairs take the keep pass from 2.32 to 2.09-2.14 s (each CTA reads
-// half as many operand bytes into shared memory per MMA), while clusters of 4
-// were no faster than single CTAs. The other passes run few query tiles and
-// use 1.
+// point tiles by multicast); 0 = automatic: pairs for d >= 512, where the
+// MMAs set the pace (1.28M x 1024: keep pass 2.32 -> 2.09-2.14 s, each CTA
+// reading half as many operand bytes into shared memory per MMA), single
+// CTAs below, where the epilogue does (1M x 128 uint8: 410 ms single, 472 ms
+// in pairs). Clusters of 4 were no faster than single CTAs on either. The
+// other passes run few query tiles and use 1.
 static cudaError_t launch_screen(int mode, int pass, int metric, const CUtensorMap& ta, const void* prows, int64_t n,
                                  int d, const ScreenArgs& a, int cl, cudaStream_t st) {
   if (a.nq <= 0) return cudaSuccess;
-  if (cl != 1 && cl != 2 && cl != 4) cl = 2;
+  if (cl != 1 && cl != 2 && cl != 4) cl = d >= 512 ? 2 : 1;
   if (mode != SCR_KNN || pass != SCR_KEEP) cl = 1;
   if (metric == MET_IP) {
     if (mode == SCR_KNN && pass == SCR_KEEP) {
