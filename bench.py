@@ -16,11 +16,13 @@ dependent points, the cluster cut. The same JSON line carries, under
     and FP8-e4m3 traversal and exact FP32 re-rank, recall and ARI judged
     against the exact index at full n;
   * n = 1,000,000 x d = 128 uint8 (100 Zipf-weighted Gaussians + 5% noise) on
-    its Vamana graph (R 64, beam 128, k 10) and on the exact index.
+    its Vamana graph (R 64, beam 128, k 10), on an NN-Descent graph, on an
+    HCNNG graph (all searched with the same beam) and on the exact index.
 Graph builds are timed separately (build_s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload vmf1024|u8-1m|batched64|sphere384] [--quick]
+                  [--workload vmf1024|vmf1024-graph|u8-1m|batched64|sphere384]
+                  [--quick] [--graph-line-only | --exact-line-only] [--n N]
 
 Prints one JSON line (rank 0). For N > 1 (torchrun) every rank runs its own
 replica of the workload on its GPU; value = all points processed / the max
