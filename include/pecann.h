@@ -377,7 +377,8 @@ typedef struct {
  * one launch for every setting's parent array, and pointer-jumping sweeps
  * over all n_settings x n entries. If h_n_clusters (HOST, n_settings entries)
  * is not NULL it receives each setting's number of clusters and the call
- * waits for the stream. Workspace: pecann_cluster_workspace_size(n, n_settings).
+ * waits for the stream. Workspace: pecann_cluster_workspace_size(n, n_settings),
+ * which with n_settings = 1 is also enough for pecann_cluster.
  * Errors: PECANN_EINVAL for a bad setting (unknown center function,
  * n_clusters < 1 with the product center, a local center without k-NN lists)
  * -- checked on the host before any GPU work.

@@ -762,7 +762,8 @@ pecann_status pecann_cluster_workspace_size(int64_t n, int32_t n_settings, size_
   if (!bytes) return set_last_error("NULL argument"), PECANN_EINVAL;
   if (n < 1 || n >= ((int64_t)1 << 31)) return set_last_error("n out of range"), PECANN_EINVAL;
   if (n_settings < 1 || n_settings > 4096) return set_last_error("n_settings must be in 1..4096"), PECANN_EINVAL;
-  *bytes = sweep_counts_offset(n, n_settings) + (size_t)n_settings * 8;
+  // (also enough for pecann_cluster, the single-setting call)
+  *bytes = std::max(sweep_counts_offset(n, n_settings) + (size_t)n_settings * 8, HDR + cluster_ws_bytes(n));
   return PECANN_OK;
 }
 

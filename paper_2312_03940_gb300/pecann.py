@@ -349,7 +349,9 @@ def pecann_cluster(density: torch.Tensor, dep: torch.Tensor, dep_dist: torch.Ten
     _cuda(dep_dist, "dep_dist", torch.float32)
     n = density.numel()
     if ws is None:
-        ws = torch.empty(8 * n + (1 << 20), dtype=torch.uint8, device=density.device)
+        nb = ctypes.c_size_t(0)
+        _check(load_library().pecann_cluster_workspace_size(n, 1, ctypes.byref(nb)))
+        ws = torch.empty(nb.value, dtype=torch.uint8, device=density.device)
     labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=density.device)
     nc = ctypes.c_int64(0)
     _check(load_library().pecann_cluster(n, _ptr(density), _ptr(dep), _ptr(dep_dist), ctypes.byref(p),
