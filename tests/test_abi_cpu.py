@@ -169,3 +169,15 @@ def test_hcnng_checks_on_host(lib):
     call = lib.pecann_build_hcnng
     assert call(ctypes.byref(ds), ctypes.byref(p), 3, 200, 3, None, None, None, g, 1 << 40, None) == pc.EINVAL
     assert call(ctypes.byref(ds), ctypes.byref(p), 3, 200, 3, g, None, None, g, 64, None) == pc.ENOMEM
+
+
+def test_cluster_workspace_size_covers_the_single_setting_call(lib):
+    """pecann_cluster accepts a workspace of pecann_cluster_workspace_size(n, 1)
+    bytes (answered on the host: past the size check the call needs a GPU)."""
+    p = pc.params(n_clusters=3)
+    g = ctypes.c_void_p(256)
+    for n in (10, 1000, 1_000_000):
+        b = ctypes.c_size_t(0)
+        assert lib.pecann_cluster_workspace_size(n, 1, ctypes.byref(b)) == pc.OK
+        assert lib.pecann_cluster(n, g, g, g, ctypes.byref(p), g, None, g, b.value, None) != pc.ENOMEM
+        assert lib.pecann_cluster(n, g, g, g, ctypes.byref(p), g, None, g, 64, None) == pc.ENOMEM
