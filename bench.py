@@ -509,14 +509,17 @@ def run_ours(args):
                                   "sample": (f"oracle brute-force index (exact k-NN + kth density) of {CPU_SAMPLE} "
                                              f"sampled points over all {n:,} rows of the same workload; the "
                                              f"dependent step is not in the sample (an upper bound)")}
-        # ---- variants: the same rows on a Vamana graph, FP32 / BF16 / FP8 traversal
-        result["variants"] = vmf_graph_variants(args, X, Xd, knn_dist, exact_labels, dev, stream, threads)
-        del path
-        torch.cuda.empty_cache()
-        # ---- the uint8 workload on its graph and on the exact index
-        del Xd, ds
-        torch.cuda.empty_cache()
-        result["variants"] += u8_variants(args, dev, stream, threads)
+        # the report lines run on one GPU only: a multi-GPU run measures the
+        # benchmark line's replicas, whose ranks would otherwise wait meanwhile
+        if world == 1:
+            # ---- variants: the same rows on a Vamana graph, FP32 / BF16 / FP8 traversal
+            result["variants"] = vmf_graph_variants(args, X, Xd, knn_dist, exact_labels, dev, stream, threads)
+            del path
+            torch.cuda.empty_cache()
+            # ---- the uint8 workload on its graph and on the exact index
+            del Xd, ds
+            torch.cuda.empty_cache()
+            result["variants"] += u8_variants(args, dev, stream, threads)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist:
