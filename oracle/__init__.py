@@ -78,6 +78,10 @@ def _load():
         _lib.orc_hcnng_partition.restype = i64
         _lib.orc_hcnng_leaf_mst.argtypes = [P, vp, i64, i32, vp]
         _lib.orc_hcnng_leaf_mst.restype = i64
+        _lib.orc_splitmix64.argtypes = [u64]
+        _lib.orc_splitmix64.restype = u64
+        _lib.orc_hcnng_draw.argtypes = [u64, i32, i64, i64, i32]
+        _lib.orc_hcnng_draw.restype = u64
         _lib.orc_dependent_points.argtypes = [P, vp, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp,
                                               ctypes.c_int]
         _lib.orc_dependent_points.restype = ctypes.c_int
@@ -230,6 +234,16 @@ def hcnng(P: Points, repeats: int, leaf_size: int, mst_deg: int, alpha: float, R
     if rc:
         raise ValueError("orc_hcnng: bad arguments")
     return dict(G=G, leaves=leaves)
+
+
+def splitmix64(x: int) -> int:
+    """SplitMix64's output for the state x (the HCNNG pivot generator)."""
+    return int(_load().orc_splitmix64(x))
+
+
+def hcnng_draw(seed: int, t: int, b: int, m: int, j: int) -> int:
+    """Draw j of the HCNNG node [b, b + m) of tree t."""
+    return int(_load().orc_hcnng_draw(seed, t, b, m, j))
 
 
 def hcnng_partition(P: Points, t: int, leaf_size: int, seed: int = 0):

@@ -1307,6 +1307,10 @@ static uint64_t hc_draw(uint64_t seed, int32_t t, int64_t b, int64_t m, int j) {
   return sm64(v + (uint64_t)j);
 }
 
+/* For the tests: the generator's output for a state, and a node's draw. */
+uint64_t orc_splitmix64(uint64_t x) { return sm64(x); }
+uint64_t orc_hcnng_draw(uint64_t seed, int32_t t, int64_t b, int64_t m, int32_t j) { return hc_draw(seed, t, b, m, j); }
+
 /* The leaves of tree t: order (n ids) and leaf_begin (n_leaves + 1 offsets,
    in the order the leaves lie in `order`). Returns the number of leaves. */
 int64_t orc_hcnng_partition(const orc_points* P, int32_t t, int32_t leaf_size, uint64_t seed, int32_t* order,

@@ -780,3 +780,29 @@ def test_hcnng_graph_invariants_and_recall():
     _, ed = exact.exact_knn(X, 10)
     o = oracle.knn_density(P, G, L=64, k=10)
     assert exact.knn_recall(o["dist"], ed) >= 0.95
+
+
+def test_hcnng_pivot_generator_is_splitmix64():
+    """The published SplitMix64 outputs for the states 0, 1 and 2 golden-ratio
+    increments (Steele, Lea and Flood's generator as distributed with xoshiro)."""
+    gold = 0x9E3779B97F4A7C15
+    assert oracle.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(gold) == 0x6E789E6AA1B965F4
+    assert oracle.splitmix64((2 * gold) % (1 << 64)) == 0x06C45D188009454F
+
+
+def test_hcnng_first_split_by_brute_force():
+    """The root split of a 60-point set into leaves of at most 40: the pivots
+    are the drawn positions of 0..59, every point is on the side of its nearer
+    pivot (ties left), and each side keeps ascending ids."""
+    X = np.random.default_rng(46).normal(size=(60, 8)).astype(np.float32)
+    P = oracle.Points(X)
+    seed, t = 12, 2  # a root split of 21 / 39 points: both sides are leaves
+    i1 = oracle.hcnng_draw(seed, t, 0, 60, 0) % 60
+    i2 = oracle.hcnng_draw(seed, t, 0, 60, 1) % 59
+    i2 += i2 >= i1
+    left = [x for x in range(60) if oracle.dis(P, x, i1) <= oracle.dis(P, x, i2)]
+    right = [x for x in range(60) if x not in left]
+    assert 0 < len(left) <= 40 and 0 < len(right) <= 40
+    L = oracle.hcnng_partition(P, t, leaf_size=40, seed=seed)
+    assert [l.tolist() for l in L] == [left, right]
